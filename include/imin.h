@@ -1,0 +1,213 @@
+/*
+ * imin.h -- C ABI of the GB300 influence-minimisation library.
+ *
+ * The library computes the data-parallel hot path of the Sandwich method for
+ * Influence Minimization by node blocking (arXiv 2405.12871): Monte Carlo
+ * live-edge worlds of the Independent Cascade model traversed from the seed
+ * set S with blocked nodes masked out, the per-world credit of candidate
+ * blockers under the lower bound D^L (dominator-tree subtree sizes, i.e. CP
+ * sets) and the upper bound D^U (LRR sets), and the greedy selection of k
+ * blockers under the LSBM / GSBM stopping rules, combined by Algorithm 1.
+ *
+ * Conventions for every call:
+ *   - Status: every int-returning call returns IMIN_OK (0) or one of the
+ *     imin_status codes below.  On error no output is written, except that
+ *     imin_solve may have overwritten the blocker arrays' contents.
+ *   - Ownership: input arrays are read during the call only and never kept;
+ *     the library copies what it needs.  Output arrays are allocated by the
+ *     caller.  Graphs stay resident on the device until imin_free_graph.
+ *   - Memory: host pointers unless a flag says "device" (then the pointer is a
+ *     CUDA device address on the context's device).
+ *   - Streams: all device work of a context runs on the stream given to
+ *     imin_create (NULL = the legacy default stream); every call returns after
+ *     its work has completed.  A context must not be used from two host
+ *     threads at once.
+ *   - Determinism: results are a pure function of (graph, S, blocked or k,
+ *     eps, delta, options).  They do not depend on launch configuration,
+ *     batching or co-scheduled work, because world j of stream (key, tag,
+ *     inst) is addressed by index: edge e is live in world j iff
+ *         (w >> 8) < ceil(p_e * 2^24),  w = word (e & 3) of
+ *         Philox4x32-10(ctr = {e >> 2, j, tag, inst}, key = {lo32(key), hi32(key)})
+ *     (Sec. 2.1: a realization keeps edge e with probability p(e)).
+ */
+#ifndef IMIN_H
+#define IMIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum imin_status {
+    IMIN_OK = 0,
+    IMIN_EINVAL = 1,    /* malformed input: row_ptr not monotone, col out of range, p NaN or
+                           outside [0,1], duplicate or out-of-range seeds, blocked node in S,
+                           k < 1, eps or delta outside (0,1), beta or gamma outside (0,1) */
+    IMIN_ERANGE = 2,    /* size limit: n >= 2^31 - 1, m >= 2^31 - 4, a world index >= 2^32,
+                           or a per-world structure larger than the library supports */
+    IMIN_ENOMEM = 3,    /* device memory budget exceeded, or an allocation failed */
+    IMIN_EDEVICE = 4,   /* CUDA error (message available through imin_last_error) */
+    IMIN_ETIMEOUT = 5   /* a bounded device-side wait expired */
+};
+
+/* Sampling mode bits for imin_sample_opts.mode. */
+enum imin_mode {
+    IMIN_REACH = 1,           /* reach[v] = number of worlds whose reach set contains v      */
+    IMIN_CREDIT_LOWER = 2,    /* credit_lower[v] = sum over worlds of |N_phi(v)| (Sec. 3.2),
+                                 the dominator-tree subtree size of v (Algorithm 2)         */
+    IMIN_CREDIT_UPPER = 4,    /* credit_upper[v] = number of worlds whose LRR set holds v
+                                 (Algorithm 3, Definition 4.2)                              */
+    IMIN_OUT_DEVICE = 0x100   /* output arrays are device pointers                         */
+};
+
+/* Solve variants (Algorithm 1 and Sec. 6's SandIMIN-). */
+enum imin_variant {
+    IMIN_SANDIMIN = 0,        /* B_L (LSBM), B_U (GSBM), B_R (LHGA), argmin of the final estimate */
+    IMIN_SANDIMIN_MINUS = 1,  /* without GSBM (alpha_2 = 0)                                  */
+    IMIN_LSBM = 2,            /* lower-bound maximisation only                                */
+    IMIN_GSBM = 3,            /* upper-bound maximisation only                                */
+    IMIN_LHGA = 4             /* heuristic only                                              */
+};
+
+typedef struct imin_ctx imin_ctx;       /* opaque, library-owned */
+typedef struct imin_graph imin_graph;   /* opaque, library-owned, device-resident */
+
+/* Create a context on CUDA device `device`.  device_mem_budget caps the bytes
+ * the context allocates on the device (0 = no cap beyond the device's free
+ * memory).  stream is a cudaStream_t (NULL = legacy default stream).
+ * Errors: IMIN_EINVAL (bad device), IMIN_EDEVICE. */
+int imin_create(imin_ctx **out, int device, size_t device_mem_budget, void *stream);
+
+/* Destroy a context and every buffer it owns.  Graphs loaded through it must
+ * have been freed first.  NULL is ignored. */
+void imin_destroy(imin_ctx *ctx);
+
+/* Load a directed graph G = (V, E, p) (Sec. 2.1) in CSR-by-source form and keep
+ * it resident on the device.
+ *   n        number of nodes, 1 <= n < 2^31 - 1
+ *   m        number of edges, 0 <= m < 2^31 - 4
+ *   row_ptr  host int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col      host int32[m], targets in [0, n); self-loops and multi-edges allowed
+ *            (each edge is an independent coin)
+ *   prob     host float[m], p(u, v) in [0, 1]
+ * The library derives the coin thresholds ceil(p * 2^24) and the in-edge
+ * (reverse) index on the device.  Errors: IMIN_EINVAL, IMIN_ERANGE,
+ * IMIN_ENOMEM, IMIN_EDEVICE. */
+int imin_load_graph(imin_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr,
+                    const int32_t *col, const float *prob, imin_graph **out);
+
+/* Release a graph.  NULL is ignored. */
+void imin_free_graph(imin_graph *g);
+
+/* Options of imin_sample.  Worlds [first_sample, first_sample + theta) of the
+ * stream (key, tag, inst) are drawn. */
+typedef struct imin_sample_opts {
+    uint64_t key;           /* Philox key */
+    uint32_t tag;           /* stream tag (the solve uses 0..7; see imin_solve) */
+    uint32_t inst;          /* instance id (lets independent queries use disjoint streams) */
+    uint64_t first_sample;  /* index of the first world */
+    uint32_t mode;          /* IMIN_REACH | IMIN_CREDIT_LOWER | IMIN_CREDIT_UPPER [| IMIN_OUT_DEVICE] */
+    uint32_t reserved;      /* must be 0 */
+} imin_sample_opts;
+
+/* Outputs of imin_sample.  Arrays are caller-allocated (host, or device with
+ * IMIN_OUT_DEVICE), NULL = not requested; requested arrays are OVERWRITTEN. */
+typedef struct imin_sample_out {
+    uint64_t *reach;          /* [n], needs IMIN_REACH */
+    uint64_t *credit_lower;   /* [n], needs IMIN_CREDIT_LOWER; 0 for seeds */
+    uint64_t *credit_upper;   /* [n], needs IMIN_CREDIT_UPPER; 0 for seeds */
+    uint32_t *world_spread;   /* [theta]: |R_j| of each world, seeds included */
+    uint64_t total_spread;    /* sum over worlds of |R_j| (seeds count: I_phi(S), Sec. 2.1) */
+    uint64_t edges_scanned;   /* sum over worlds of the out-degrees of reached nodes */
+    uint64_t nonempty_lrr;    /* worlds whose Global Sampling target was reached (Algorithm 3) */
+} imin_sample_out;
+
+/* Monte Carlo sampling of theta live-edge worlds from the seed set S with the
+ * blocked set B masked out (Sec. 2.1: a blocker's in-edges get p = 0).
+ * Reach counts, lower credit (Algorithm 2 / Lemma 4.1: the credit of v in
+ * world j is the number of CP sets of world j that contain v) and upper credit
+ * (Algorithm 3 / Lemma 4.2: the target t_j is uniform over V'_s -- the nodes
+ * reachable from S in G[V \ B] over edges with p > 0, minus S -- drawn as
+ * floor(r64 * |V'_s| / 2^64) with r64 = (out[1] << 32) | out[0] of
+ * Philox(ctr = {0xFFFFFFFF, j, tag, inst}) over V'_s sorted ascending; the LRR
+ * set holds the nodes of R_j \ S that reach t_j by live edges inside R_j \ S).
+ *   S, nS        host int32[nS], 1 <= nS, distinct, in [0, n)
+ *   blocked, nB  host int32[nB] (NULL if nB = 0), distinct, in [0, n), disjoint from S
+ *   theta        number of worlds, first_sample + theta <= 2^32
+ * Errors: IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM, IMIN_EDEVICE. */
+int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *blocked, int32_t nB,
+                uint64_t theta, const imin_sample_opts *opts, imin_sample_out *out);
+
+/* Options of imin_solve.  Defaults used by the paper (Sec. 6): beta = gamma = 0.1. */
+typedef struct imin_solve_opts {
+    double beta;            /* relative error of the spread estimate used by LSBM, in (0,1) */
+    double gamma;           /* relative error of the final estimates of Algorithm 1, in (0,1) */
+    uint64_t key;           /* Philox key */
+    uint32_t inst;          /* instance id (stream separation between queries) */
+    int32_t variant;        /* imin_variant */
+    uint64_t fixed_theta;   /* 0 = the paper's stopping rules; otherwise LSBM and GSBM
+                               use theta_0 = fixed_theta and a single iteration */
+} imin_solve_opts;
+
+/* Result of imin_solve.  The four arrays are caller-allocated with room for
+ * k entries each (B_L, B_U, B_R may be NULL). */
+typedef struct imin_result {
+    int32_t *blockers;      /* chosen blocker set (ascending by the order picked) */
+    int32_t *B_L, *B_U, *B_R;
+    int32_t n_blockers, nBL, nBU, nBR;
+    int32_t chosen;         /* 0 = B_L, 1 = B_U, 2 = B_R */
+    int32_t iters_L, iters_U;
+    int32_t nVs;            /* |V'_s| */
+    double I_hat;           /* (beta, delta/6)-estimate of E[I_G(s)] (Algorithm 4, line 4) */
+    double I_after[3];      /* (gamma, delta)-estimates of E[I_{G[V\B]}(s)] for B_L, B_U, B_R */
+    double sigmaL_L, sigmaU_L, sigmaL_U, sigmaU_U;   /* last sigma^L, sigma^U of LSBM / GSBM */
+    double DL_hat;          /* Cov_{C2}(B_L) / |C2| */
+    double DU_hat;          /* |V'_s| Cov_{L2}(B_U) / |L2| */
+    double ratio_lb;        /* computable approximation-ratio lower bound (Sec. 6.4) */
+    double OPT_L;           /* lower bound of D^L(B^o_L) (Sec. 5.1) */
+    double theta_max_L, theta_max_U;
+    uint64_t n_spread;      /* worlds drawn for I_hat */
+    uint64_t theta_C1, theta_C2, theta_L1, theta_L2;  /* final collection sizes */
+    uint64_t n_final[3];    /* worlds drawn for each final estimate */
+    uint64_t covC2, covL2;  /* Cov_{C2}(B_L), Cov_{L2}(B_U) */
+    uint64_t edges_scanned; /* forward edges scanned over the whole solve */
+    uint64_t worlds_sampled;/* worlds traversed over the whole solve (incl. speculative ones) */
+    double ms_stage[8];     /* wall time per stage: 0 I_hat, 1 LSBM sampling, 2 LSBM greedy,
+                               3 GSBM sampling, 4 GSBM greedy, 5 final estimates, 6 host, 7 total */
+    double kernel_ms[4];    /* device time (CUDA events on the context's stream) of the world
+                               kernel launches: 0 reach-only (the stopping-rule estimates of
+                               I_hat and of the three final candidates), 1 lower-bound sampling,
+                               2 upper-bound sampling; 3 the greedy rounds */
+    uint64_t reach_nodes;   /* nodes reached by the reach-only launches (seeds included) */
+    uint64_t reach_edges;   /* edges scanned by the reach-only launches */
+    uint64_t reach_launches;/* reach-only world-kernel launches */
+    uint64_t kernel_launches; /* kernels the library launched during the call */
+} imin_result;
+
+/* Influence Minimization (problem statement, Sec. 2.1): choose at most k
+ * blockers from V \ S by Algorithm 1 (LSBM Algorithm 4, GSBM Sec. 5.2, LHGA
+ * Sec. 5.3).  Stream tags: 0 spread estimate, 1/2 CP collections C1/C2,
+ * 3/4 LRR collections L1/L2, 5/6/7 final estimates of B_L/B_U/B_R.
+ *   S, nS   host int32[nS], distinct, in [0, n), nS >= 1
+ *   k       1 <= k < n - nS
+ *   eps     in (0, 1); delta in (0, 1) (the paper uses delta = 1/n)
+ * When the out-neighbours ON of S number at most k, ON is returned for every
+ * candidate without sampling (Algorithm 4, lines 2-3).
+ * Errors: IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM, IMIN_EDEVICE, IMIN_ETIMEOUT. */
+int imin_solve(imin_graph *g, const int32_t *S, int32_t nS, int32_t k, double eps, double delta,
+               const imin_solve_opts *opts, imin_result *res);
+
+/* Static description of a status code. */
+const char *imin_strerror(int status);
+
+/* Copy the context's last error message (NUL-terminated, truncated to len). */
+void imin_last_error(imin_ctx *ctx, char *buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IMIN_H */

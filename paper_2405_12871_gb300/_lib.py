@@ -1,0 +1,256 @@
+"""Thin ctypes binding of the C ABI in ``include/imin.h``.
+
+Argument marshalling only: every step of the sampling and the solve runs in
+the CUDA library.  If the compiled library is missing this module raises; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+IMIN_OK, IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM, IMIN_EDEVICE, IMIN_ETIMEOUT = range(6)
+IMIN_REACH, IMIN_CREDIT_LOWER, IMIN_CREDIT_UPPER, IMIN_OUT_DEVICE = 1, 2, 4, 0x100
+VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
+
+# names the library must export (checked by the CPU tests against include/imin.h)
+EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
+           "imin_solve", "imin_strerror", "imin_last_error"]
+
+
+class SampleOpts(C.Structure):
+    _fields_ = [("key", C.c_uint64), ("tag", C.c_uint32), ("inst", C.c_uint32),
+                ("first_sample", C.c_uint64), ("mode", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class SampleOut(C.Structure):
+    _fields_ = [("reach", C.c_void_p), ("credit_lower", C.c_void_p),
+                ("credit_upper", C.c_void_p), ("world_spread", C.c_void_p),
+                ("total_spread", C.c_uint64), ("edges_scanned", C.c_uint64),
+                ("nonempty_lrr", C.c_uint64)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("beta", C.c_double), ("gamma", C.c_double), ("key", C.c_uint64),
+                ("inst", C.c_uint32), ("variant", C.c_int32), ("fixed_theta", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("blockers", C.POINTER(C.c_int32)), ("B_L", C.POINTER(C.c_int32)),
+        ("B_U", C.POINTER(C.c_int32)), ("B_R", C.POINTER(C.c_int32)),
+        ("n_blockers", C.c_int32), ("nBL", C.c_int32), ("nBU", C.c_int32), ("nBR", C.c_int32),
+        ("chosen", C.c_int32), ("iters_L", C.c_int32), ("iters_U", C.c_int32),
+        ("nVs", C.c_int32),
+        ("I_hat", C.c_double), ("I_after", C.c_double * 3), ("sigmaL_L", C.c_double),
+        ("sigmaU_L", C.c_double), ("sigmaL_U", C.c_double), ("sigmaU_U", C.c_double),
+        ("DL_hat", C.c_double), ("DU_hat", C.c_double), ("ratio_lb", C.c_double),
+        ("OPT_L", C.c_double), ("theta_max_L", C.c_double), ("theta_max_U", C.c_double),
+        ("n_spread", C.c_uint64), ("theta_C1", C.c_uint64), ("theta_C2", C.c_uint64),
+        ("theta_L1", C.c_uint64), ("theta_L2", C.c_uint64), ("n_final", C.c_uint64 * 3),
+        ("covC2", C.c_uint64), ("covL2", C.c_uint64), ("edges_scanned", C.c_uint64),
+        ("worlds_sampled", C.c_uint64), ("ms_stage", C.c_double * 8),
+        ("kernel_ms", C.c_double * 4), ("reach_nodes", C.c_uint64), ("reach_edges", C.c_uint64),
+        ("reach_launches", C.c_uint64), ("kernel_launches", C.c_uint64),
+    ]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libimin.so (building it with nvcc first when it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"CUDA library not built: {path}")
+        _build.build()
+    L = C.CDLL(path)
+    P = C.POINTER
+    L.imin_create.argtypes = [P(C.c_void_p), C.c_int, C.c_size_t, C.c_void_p]
+    L.imin_create.restype = C.c_int
+    L.imin_destroy.argtypes = [C.c_void_p]
+    L.imin_destroy.restype = None
+    L.imin_load_graph.argtypes = [C.c_void_p, C.c_int32, C.c_int64, P(C.c_int32), P(C.c_int32),
+                                  P(C.c_float), P(C.c_void_p)]
+    L.imin_load_graph.restype = C.c_int
+    L.imin_free_graph.argtypes = [C.c_void_p]
+    L.imin_free_graph.restype = None
+    L.imin_sample.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), C.c_int32,
+                              C.c_uint64, P(SampleOpts), P(SampleOut)]
+    L.imin_sample.restype = C.c_int
+    L.imin_solve.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, C.c_int32, C.c_double,
+                             C.c_double, P(SolveOpts), P(Result)]
+    L.imin_solve.restype = C.c_int
+    L.imin_strerror.argtypes = [C.c_int]
+    L.imin_strerror.restype = C.c_char_p
+    L.imin_last_error.argtypes = [C.c_void_p, C.c_char_p, C.c_size_t]
+    L.imin_last_error.restype = None
+    _lib = L
+    return L
+
+
+class IminError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+def _i32p(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None and a.size else None
+
+
+def _as_i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+# --- the C ABI, one Python function per entry point ---------------------------------
+
+def imin_create(device: int = 0, device_mem_budget: int = 0, stream: int = 0):
+    L = load()
+    h = C.c_void_p()
+    rc = L.imin_create(C.byref(h), int(device), int(device_mem_budget), C.c_void_p(stream or None))
+    if rc != IMIN_OK:
+        raise IminError(rc, "imin_create: " + L.imin_strerror(rc).decode())
+    return h
+
+
+def imin_destroy(ctx):
+    load().imin_destroy(ctx)
+
+
+def imin_last_error(ctx) -> str:
+    buf = C.create_string_buffer(1024)
+    load().imin_last_error(ctx, buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(ctx, rc, what):
+    if rc != IMIN_OK:
+        raise IminError(rc, f"{what}: {load().imin_strerror(rc).decode()}: {imin_last_error(ctx)}")
+
+
+def imin_load_graph(ctx, n, row_ptr, col, prob):
+    L = load()
+    row_ptr = _as_i32(row_ptr)
+    col = _as_i32(col)
+    prob = np.ascontiguousarray(np.asarray(prob, dtype=np.float32))
+    g = C.c_void_p()
+    rc = L.imin_load_graph(ctx, int(n), int(col.shape[0]), _i32p(row_ptr),
+                           col.ctypes.data_as(C.POINTER(C.c_int32)),
+                           prob.ctypes.data_as(C.POINTER(C.c_float)), C.byref(g))
+    _check(ctx, rc, "imin_load_graph")
+    return g
+
+
+def imin_free_graph(g):
+    load().imin_free_graph(g)
+
+
+def imin_sample(ctx, g, n, S, blocked=(), theta=1, key=0, tag=0, inst=0, first=0,
+                mode=IMIN_REACH, out=None, per_world=False):
+    """Host outputs (numpy) unless ``out`` maps names to device pointers (then
+    IMIN_OUT_DEVICE is set and the pointers are written in place)."""
+    L = load()
+    S = _as_i32(S)
+    B = _as_i32(blocked)
+    opts = SampleOpts(int(key), int(tag), int(inst), int(first), int(mode), 0)
+    so = SampleOut()
+    res = {}
+    if out is None:
+        for name, bit in (("reach", IMIN_REACH), ("credit_lower", IMIN_CREDIT_LOWER),
+                          ("credit_upper", IMIN_CREDIT_UPPER)):
+            if mode & bit:
+                res[name] = np.zeros(n, np.uint64)
+                setattr(so, name, res[name].ctypes.data)
+        if per_world:
+            res["world_spread"] = np.zeros(max(int(theta), 1), np.uint32)
+            so.world_spread = res["world_spread"].ctypes.data
+    else:
+        opts.mode |= IMIN_OUT_DEVICE
+        for name, ptr in out.items():
+            setattr(so, name, int(ptr))
+    rc = L.imin_sample(g, _i32p(S), len(S), _i32p(B), len(B), int(theta), C.byref(opts),
+                       C.byref(so))
+    _check(ctx, rc, "imin_sample")
+    res.update(total_spread=int(so.total_spread), edges_scanned=int(so.edges_scanned),
+               nonempty_lrr=int(so.nonempty_lrr))
+    if "world_spread" in res:
+        res["world_spread"] = res["world_spread"][: int(theta)]
+    return res
+
+
+def imin_solve(ctx, g, S, k, eps, delta, beta=0.1, gamma=0.1, key=0, inst=0,
+               variant="sandimin", fixed_theta=0):
+    L = load()
+    S = _as_i32(S)
+    arrs = [np.zeros(max(int(k), 1), np.int32) for _ in range(4)]
+    r = Result()
+    r.blockers, r.B_L, r.B_U, r.B_R = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
+    opts = SolveOpts(float(beta), float(gamma), int(key), int(inst), VARIANTS[variant],
+                     int(fixed_theta))
+    rc = L.imin_solve(g, _i32p(S), len(S), int(k), float(eps), float(delta), C.byref(opts),
+                      C.byref(r))
+    _check(ctx, rc, "imin_solve")
+    d = {}
+    for name, _ in Result._fields_:
+        if name in ("blockers", "B_L", "B_U", "B_R"):
+            continue
+        v = getattr(r, name)
+        d[name] = list(v) if hasattr(v, "__len__") else v
+    d["blockers"] = arrs[0][: r.n_blockers].copy()
+    d["B_L"] = arrs[1][: r.nBL].copy()
+    d["B_U"] = arrs[2][: r.nBU].copy()
+    d["B_R"] = arrs[3][: r.nBR].copy()
+    return d
+
+
+class Context:
+    """Convenience owner of an imin_ctx (and the graphs loaded through it)."""
+
+    def __init__(self, device=0, device_mem_budget=0, stream=0):
+        self.h = imin_create(device, device_mem_budget, stream)
+
+    def load_graph(self, g):
+        return Graph(self, g)
+
+    def close(self):
+        if self.h:
+            imin_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Graph:
+    def __init__(self, ctx: Context, g):
+        self.ctx = ctx
+        self.n = int(g.n)
+        self.m = int(g.m)
+        self.h = imin_load_graph(ctx.h, g.n, g.row_ptr, g.col, g.prob)
+
+    def sample(self, S, blocked=(), theta=1, **kw):
+        return imin_sample(self.ctx.h, self.h, self.n, S, blocked, theta, **kw)
+
+    def solve(self, S, k, eps, delta, **kw):
+        return imin_solve(self.ctx.h, self.h, S, k, eps, delta, **kw)
+
+    def free(self):
+        if self.h:
+            imin_free_graph(self.h)
+            self.h = None

@@ -1,0 +1,200 @@
+// common.cuh -- internal declarations shared by the library's translation units.
+//
+// Device-side layout (all resident in HBM):
+//   graph:  row_ptr int32[n+1]; col int32[m4]; thr uint32[m4] (m4 = m rounded up to a
+//           multiple of 4, padding thr = 0), so that one 16-byte load brings the 4 edges
+//           of one Philox counter group;  reverse index in_ptr int32[n+1], in_src int32[m],
+//           in_eid int32[m], in_thr uint32[m] (thr of the forward edge, for coalescing).
+//   slots:  one per resident warp of the world kernel (a warp traverses one world at a
+//           time): visited bitmap (n bits), BFS queue (qcap), and for the lower bound
+//           node->local map (n), per-local arrays (qcap) and live-edge pairs (ecap).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/imin.h"
+
+#define IMIN_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 -> 64-bit
+// products on words 0 and 2, high halves mixed with words 1, 3 and the round
+// key; the key advances by the two Weyl constants after each round.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t pick_word(const uint4 &w, int i)
+{
+    return i == 0 ? w.x : (i == 1 ? w.y : (i == 2 ? w.z : w.w));
+}
+
+// ---------------------------------------------------------------------------
+// Error handling
+// ---------------------------------------------------------------------------
+struct ImError {
+    int code;
+    std::string msg;
+};
+
+#define IM_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t _e = (call);                                                           \
+        if (_e != cudaSuccess)                                                             \
+            throw ImError{IMIN_EDEVICE, std::string(#call) + ": " + cudaGetErrorString(_e)}; \
+    } while (0)
+
+// process-wide count of kernels the library launched (reported per call)
+extern unsigned long long g_kernel_launches;
+#define IM_CHECK_LAUNCH()                 \
+    do {                                  \
+        ++g_kernel_launches;              \
+        IM_CUDA(cudaGetLastError());      \
+    } while (0)
+
+// Device-side error flags (bit set by kernels, read by the host after a launch).
+enum : uint32_t {
+    DERR_TIMEOUT = 1u,    // a bounded iteration gave up
+    DERR_INTERNAL = 2u,   // an invariant failed (index out of range)
+};
+
+// ---------------------------------------------------------------------------
+// Device memory: grow-only buffers charged against the context's budget.
+// ---------------------------------------------------------------------------
+struct imin_ctx;
+
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    imin_ctx *ctx = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release();
+    // ensure capacity (contents are NOT preserved unless keep = true)
+    void ensure(imin_ctx *c, size_t need, bool keep = false);
+    template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct imin_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t budget = 0;      // 0 = none
+    size_t in_use = 0;
+    int num_sms = 0;
+    std::string last_error;
+    // scratch shared by calls (grow-only)
+    DBuf slots;             // world-kernel slot arena
+    DBuf big_slots;         // slots for deferred (oversized) worlds
+    size_t slots_layout = 0, big_slots_layout = 0;
+    DBuf misc;              // small per-call device scalars
+    DBuf hostpin_dummy;
+    unsigned long long *h_misc = nullptr;  // pinned host mirror of `misc` scalars
+};
+
+void *dev_alloc(imin_ctx *ctx, size_t bytes);
+void dev_free(imin_ctx *ctx, void *p, size_t bytes);
+
+// ---------------------------------------------------------------------------
+// Graph
+// ---------------------------------------------------------------------------
+struct imin_graph {
+    imin_ctx *ctx = nullptr;
+    int32_t n = 0;
+    int64_t m = 0, m4 = 0;
+    // device
+    DBuf row_ptr, col, thr, in_ptr, in_src, in_eid, in_thr;
+    // host copies used by the controller (ON, q(v), out-degrees, V'_s)
+    std::vector<int32_t> h_row_ptr, h_col;
+    std::vector<uint32_t> h_thr;
+};
+
+// ---------------------------------------------------------------------------
+// World kernel interface (sampler.cu)
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    WF_REACH = 1u,       // reach[v] += 1
+    WF_LOWER = 2u,       // dominator tree + credit_L
+    WF_UPPER = 4u,       // LRR set + credit_U
+    WF_STORE = 8u,       // store CP records / LRR sets
+    WF_SPREAD = 16u,     // world_spread[rel] = |R_j|
+    WF_STOP = 32u,       // stop claiming worlds once the running spread reaches stop_T
+};
+
+struct SlotCfg {
+    int warps = 0;          // number of slots (= resident warps of the launch)
+    int32_t qcap = 0;       // queue / local-array capacity per slot
+    int32_t ecap = 0;       // live-edge pair capacity per slot (lower bound only)
+    size_t bm_words = 0;    // 32-bit words of one visited bitmap
+    bool lower = false, upper = false;
+    size_t bytes_per_slot() const;
+};
+
+// Outputs / stores written by the world kernel.
+struct WorldOut {
+    unsigned long long *reach = nullptr, *credit_L = nullptr, *credit_U = nullptr;
+    uint32_t *world_spread = nullptr;        // indexed by relative world index
+    unsigned long long *acc = nullptr;       // [0] spread, [1] edges, [2] nonempty LRR,
+                                             // [3] running spread (stop rule), [4] worlds done
+    unsigned long long stop_T = 0;
+    uint32_t *deferred = nullptr;            // relative indices of worlds to redo
+    uint32_t *n_deferred = nullptr;
+    uint32_t deferred_cap = 0;
+    uint32_t *err = nullptr;
+    // CP record store (lower bound)
+    int32_t *rec_node = nullptr, *rec_par = nullptr, *rec_size = nullptr;
+    unsigned long long *rec_cursor = nullptr;
+    unsigned long long rec_cap = 0;
+    // LRR set store (upper bound)
+    int32_t *set_elem = nullptr;
+    unsigned long long *set_off = nullptr;   // [rel world]
+    uint32_t *set_len = nullptr;             // [rel world]
+    unsigned long long *set_cursor = nullptr;
+    unsigned long long set_cap = 0;
+};
+
+struct QueryDev {
+    const int32_t *S = nullptr;      // device, nS entries (distinct)
+    int32_t nS = 0;
+    const uint32_t *seed_bm = nullptr;
+    const uint32_t *blocked_bm = nullptr;   // may be null
+    const int32_t *Vs = nullptr;     // device, sorted ascending
+    int32_t nVs = 0;
+    uint64_t key = 0;
+    uint32_t tag = 0, inst = 0;
+};
+
+// Run worlds [first, first + count) (or first + list[i] for i < count when list is
+// non-null) of the stream (key, tag, inst).  Returns the number of worlds whose
+// per-warp buffers overflowed (their relative indices are in out.deferred); those
+// worlds contributed nothing.
+void launch_worlds(imin_ctx *ctx, const imin_graph *g, const QueryDev &q, uint32_t flags,
+                   uint64_t first, uint32_t count, const uint32_t *list, const SlotCfg &cfg,
+                   void *slot_base, const WorldOut &out, uint32_t *claim_counter);
+
+// ---------------------------------------------------------------------------
+// Utilities (graph.cu)
+// ---------------------------------------------------------------------------
+// exclusive scan of n int64 values in place (d_tmp: >= scan_tmp_bytes(n) bytes)
+size_t scan_tmp_bytes(int64_t n);
+void exclusive_scan_i64(imin_ctx *ctx, long long *d, int64_t n, void *d_tmp);
+void exclusive_scan_i32(imin_ctx *ctx, int32_t *d, int64_t n, void *d_tmp);
+void fill_bitmap(imin_ctx *ctx, uint32_t *bm, size_t words, const int32_t *d_nodes, int32_t cnt);

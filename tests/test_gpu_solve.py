@@ -1,0 +1,90 @@
+"""GPU parity of imin_solve (Algorithm 1 with LSBM, GSBM, LHGA) against the
+oracle: blockers, candidate sets, sample counts chosen by the stopping rules,
+and every bound estimate -- bit for bit (the host math runs the same IEEE
+operations in the same order on the same integers)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import gpu_ctx
+from paper_2405_12871_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FIELDS_INT = ["n_blockers", "nBL", "nBU", "nBR", "chosen", "iters_L", "iters_U", "nVs",
+              "n_spread", "theta_C1", "theta_C2", "theta_L1", "theta_L2", "n_final", "covC2",
+              "covL2"]
+FIELDS_F = ["I_hat", "I_after", "sigmaL_L", "sigmaU_L", "sigmaL_U", "sigmaU_U", "DL_hat",
+            "DU_hat", "ratio_lb", "OPT_L", "theta_max_L", "theta_max_U"]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gpu_ctx()
+    yield c
+    c.close()
+
+
+def compare(got, want):
+    for f in ("blockers", "B_L", "B_U", "B_R"):
+        assert list(got[f]) == list(want[f]), (f, list(got[f]), list(want[f]))
+    for f in FIELDS_INT:
+        assert got[f] == want[f], (f, got[f], want[f])
+    for f in FIELDS_F:
+        assert got[f] == want[f], (f, got[f], want[f])
+
+
+@pytest.mark.parametrize("variant", ["sandimin", "sandimin-", "lsbm", "gsbm", "lhga"])
+def test_er1k_fixed_theta(ctx, variant):
+    g, S, cfg = synth.workload_er1k()
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=cfg["k"], eps=0.2, delta=1.0 / g.n, variant=variant, fixed_theta=cfg["theta"])
+    compare(G.solve(S, **kw), og.solve(S, **kw))
+    G.free()
+
+
+@pytest.mark.parametrize("eps,k", [(0.2, 5), (0.5, 3), (0.1, 10)])
+def test_er1k_stopping_rules(ctx, eps, k):
+    g, S, cfg = synth.workload_er1k()
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=k, eps=eps, delta=1.0 / g.n)
+    compare(G.solve(S, **kw), og.solve(S, **kw))
+    G.free()
+
+
+def test_small_chung_lu_solve(ctx):
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
+    S = synth.seeds_top_outdeg(g, 10, 0.01, seed=4)
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=20, eps=0.3, delta=1.0 / g.n, key=3)
+    compare(G.solve(S, **kw), og.solve(S, **kw))
+    G.free()
+
+
+def test_chain_and_on_shortcut(ctx):
+    n = 12
+    edges = [(0, 1), (0, 2), (1, 3), (2, 3)] + [(3, i) for i in range(4, n)]
+    g = synth.csr_from_edges(n, [e[0] for e in edges], [e[1] for e in edges])
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    r = G.solve([0], k=1, eps=0.2, delta=0.05)
+    compare(r, og.solve([0], k=1, eps=0.2, delta=0.05))
+    assert list(r["blockers"]) == [3]
+    r = G.solve([0], k=2, eps=0.2, delta=0.05)
+    assert list(r["blockers"]) == [1, 2] and r["n_spread"] == 0
+    G.free()
+
+
+def test_solve_validation(ctx):
+    from paper_2405_12871_gb300 import _lib
+    g, S, cfg = synth.workload_er1k()
+    G = ctx.load_graph(g)
+    for kw in (dict(k=0, eps=0.2, delta=0.01), dict(k=5, eps=1.0, delta=0.01),
+               dict(k=5, eps=0.2, delta=0.0), dict(k=5, eps=0.2, delta=0.01, beta=1.5)):
+        with pytest.raises(_lib.IminError) as e:
+            G.solve(S, **kw)
+        assert e.value.code == _lib.IMIN_EINVAL
+    G.free()
