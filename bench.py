@@ -182,6 +182,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--reach-only-worlds", type=int, default=0,
+                    help="profiling case: run two imin_sample launches of this many reach-only "
+                         "worlds on the same workload (the stopping rule's kernel) and exit")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -202,6 +205,19 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = _lib.Context(local, stream=stream.cuda_stream)
     G = ctx.load_graph(g)
+    if args.reach_only_worlds:
+        th = args.reach_only_worlds
+        for it in range(2):
+            torch.cuda.synchronize()
+            a = time.perf_counter()
+            r = G.sample(S, theta=th, key=0, tag=0, first=it * th, mode=0)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - a
+            print(json.dumps({"reach_only_worlds": th, "s": dt, "nodes": r["total_spread"],
+                              "edges": r["edges_scanned"], "gteps": r["edges_scanned"] / dt / 1e9}))
+        G.free()
+        ctx.close()
+        return 0
     inst = rank                                   # independent replica per rank
     kw = dict(k=cfg["k"], eps=cfg["eps"], delta=cfg["delta"], key=cfg["key"], inst=inst)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

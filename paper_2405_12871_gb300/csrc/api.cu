@@ -234,7 +234,12 @@ struct Runner {
             }
             c.qcap = std::min<int32_t>(n + 1, std::max<int32_t>(q, nS + 1));
             c.ecap = c.lower ? std::min<int64_t>(std::max<int64_t>(g->m, 1), 2 * (int64_t)c.qcap) : 0;
-            const int per_sm = c.lower ? 8 : 32;
+            int per_sm = c.lower ? 8 : 32;
+            // tuning hook: IMIN_SLOT_WARPS_PER_SM overrides the resident warps per SM
+            if (const char *env = std::getenv("IMIN_SLOT_WARPS_PER_SM")) {
+                const long v = std::strtol(env, nullptr, 10);
+                if (v >= 1 && v <= 64) per_sm = (int)v;
+            }
             c.warps = ctx->num_sms * per_sm;
         }
         // never use more than half of the free device memory for slots
