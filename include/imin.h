@@ -206,6 +206,42 @@ const char *imin_strerror(int status);
 /* Copy the context's last error message (NUL-terminated, truncated to len). */
 void imin_last_error(imin_ctx *ctx, char *buf, size_t len);
 
+/* ---------------------------------------------------------------------------
+ * No-allocation variant.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory -- an application whose device
+ * memory is reserved in full by its own pooling allocator (for example a
+ * framework's caching allocator or a serving process under a hard quota), or a
+ * plug-in whose host program does not let it call cudaMalloc.
+ *
+ * imin_sample_reach_noalloc draws worlds [first_sample, first_sample + theta)
+ * of the stream (key, tag, inst) exactly as imin_sample with mode IMIN_REACH
+ * does (same coins, same masked BFS from S, no blocked set) and gives the same
+ * counts.  It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * scratch is one file-scope __device__ array of IMIN_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.
+ *   d_row_ptr, d_col, d_prob  the graph in CSR form (as imin_load_graph), in
+ *                             DEVICE memory owned by the caller, n <= IMIN_NOALLOC_MAX_NODES
+ *   S, nS                     HOST int32[nS], distinct, in [0, n), 1 <= nS <= 1024
+ *   d_reach                   DEVICE uint64[n] or NULL; overwritten with reach counts
+ *   d_world_spread            DEVICE uint32[theta] or NULL; |R_j| per world
+ *   totals                    HOST uint64[2]: total spread, edges scanned
+ *   stream                    cudaStream_t of the caller's device (NULL = legacy default)
+ * The first call made with a given device current looks up the array's device
+ * address (cudaGetSymbolAddress) and keeps it; make that first call before any
+ * stream capture.  Every call reuses the same array and clears what must start
+ * at zero; calls whose GPU work overlaps (other streams, other host threads)
+ * race on the array and must be serialised by the caller.  The call returns
+ * after its work has completed.
+ * Errors: IMIN_EINVAL (NULL pointer, bad seeds), IMIN_ERANGE (n above the
+ * maximum, more than 1024 seeds, world index >= 2^32), IMIN_EDEVICE. */
+#define IMIN_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+#define IMIN_NOALLOC_MAX_NODES 2000000
+int imin_sample_reach_noalloc(const int32_t *d_row_ptr, const int32_t *d_col, const float *d_prob,
+                              int32_t n, int64_t m, const int32_t *S, int32_t nS, uint64_t theta,
+                              uint64_t key, uint32_t tag, uint32_t inst, uint64_t first_sample,
+                              uint64_t *d_reach, uint32_t *d_world_spread, uint64_t *totals,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,8 @@ VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 
 # names the library must export (checked by the CPU tests against include/imin.h)
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
-           "imin_solve", "imin_strerror", "imin_last_error"]
+           "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc"]
+NOALLOC_MAX_NODES = 2_000_000
 
 
 class SampleOpts(C.Structure):
@@ -97,6 +98,11 @@ def load(build_if_missing: bool = True):
     L.imin_strerror.restype = C.c_char_p
     L.imin_last_error.argtypes = [C.c_void_p, C.c_char_p, C.c_size_t]
     L.imin_last_error.restype = None
+    L.imin_sample_reach_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                            C.c_int64, P(C.c_int32), C.c_int32, C.c_uint64,
+                                            C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
+                                            C.c_void_p, C.c_void_p, P(C.c_uint64), C.c_void_p]
+    L.imin_sample_reach_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -254,3 +260,20 @@ class Graph:
         if self.h:
             imin_free_graph(self.h)
             self.h = None
+
+
+def imin_sample_reach_noalloc(d_row_ptr, d_col, d_prob, n, m, S, theta, key=0, tag=0, inst=0,
+                              first=0, d_reach=0, d_world_spread=0, stream=0):
+    """Reach-only sampling into caller-owned device buffers, with no device allocation
+    (pointers are integers, e.g. torch ``data_ptr()``).  Returns (total_spread, edges)."""
+    L = load()
+    S = _as_i32(S)
+    tot = (C.c_uint64 * 2)()
+    rc = L.imin_sample_reach_noalloc(C.c_void_p(d_row_ptr), C.c_void_p(d_col or None),
+                                     C.c_void_p(d_prob or None), int(n), int(m), _i32p(S), len(S),
+                                     int(theta), int(key), int(tag), int(inst), int(first),
+                                     C.c_void_p(d_reach or None), C.c_void_p(d_world_spread or None),
+                                     tot, C.c_void_p(stream or None))
+    if rc != IMIN_OK:
+        raise IminError(rc, "imin_sample_reach_noalloc: " + L.imin_strerror(rc).decode())
+    return int(tot[0]), int(tot[1])
