@@ -76,7 +76,7 @@ struct Query {
     std::vector<int32_t> S;       // sorted, distinct
     std::vector<int32_t> blocked; // sorted, distinct
     std::vector<uint8_t> is_seed, is_blocked;
-    DBuf dS, dseed_bm, dblk_bm, dVs;
+    DBuf dS, dseed_bm, dblk_bm, dB, dVs;
     std::vector<int32_t> Vs;      // sorted ascending
     size_t words = 0;
 };
@@ -139,14 +139,12 @@ void prepare_query(imin_ctx *ctx, const imin_graph *g, Query &q, const int32_t *
     q.dseed_bm.ensure(ctx, q.words * 4);
     fill_bitmap(ctx, q.dseed_bm.as<uint32_t>(), q.words, q.dS.as<int32_t>(), (int32_t)q.S.size());
     if (!q.blocked.empty()) {
-        DBuf tmp;
-        tmp.ensure(ctx, q.blocked.size() * 4);
-        IM_CUDA(cudaMemcpyAsync(tmp.p, q.blocked.data(), q.blocked.size() * 4,
+        q.dB.ensure(ctx, q.blocked.size() * 4);
+        IM_CUDA(cudaMemcpyAsync(q.dB.p, q.blocked.data(), q.blocked.size() * 4,
                                 cudaMemcpyHostToDevice, st));
         q.dblk_bm.ensure(ctx, q.words * 4);
-        fill_bitmap(ctx, q.dblk_bm.as<uint32_t>(), q.words, tmp.as<int32_t>(),
+        fill_bitmap(ctx, q.dblk_bm.as<uint32_t>(), q.words, q.dB.as<int32_t>(),
                     (int32_t)q.blocked.size());
-        IM_CUDA(cudaStreamSynchronize(st));
     }
     if (need_vs) {
         compute_Vs(g, q);
@@ -164,6 +162,8 @@ QueryDev qdev(const Query &q, uint64_t key, uint32_t tag, uint32_t inst)
     d.nS = (int32_t)q.S.size();
     d.seed_bm = q.dseed_bm.as<uint32_t>();
     d.blocked_bm = q.blocked.empty() ? nullptr : q.dblk_bm.as<uint32_t>();
+    d.B = q.blocked.empty() ? nullptr : q.dB.as<int32_t>();
+    d.nB = (int32_t)q.blocked.size();
     d.Vs = q.Vs.empty() ? nullptr : q.dVs.as<int32_t>();
     d.nVs = (int32_t)q.Vs.size();
     d.key = key;
@@ -173,24 +173,32 @@ QueryDev qdev(const Query &q, uint64_t key, uint32_t tag, uint32_t inst)
 }
 
 // ---------------------------------------------------------------------------
-// World runner: main launch + deferred worlds on large slots
+// Task runner: one persistent launch over several tasks, then the deferred
+// worlds (store room after growth on normal slots, oversized worlds on large
+// slots) until none is left.
 // ---------------------------------------------------------------------------
+struct TaskRun {
+    const imin_graph *g = nullptr;
+    QueryDev q;
+    uint64_t first = 0;
+    uint32_t count = 0;
+    WorldOut out;
+    std::function<void(uint32_t)> grow;   // enlarge the task's store for nd worlds; updates out
+    unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t claimed_main = 0;
+};
+
+constexpr size_t CTL = 128;   // per-task control block: acc[8] | n_deferred | err
+
 struct Runner {
     imin_ctx *ctx;
-    const imin_graph *g;
-    DBuf acc, claim, deferred, ndef, err;
-    unsigned long long h_acc[8];
-    uint32_t claimed_main = 0;
     double kernel_ms = 0.0;   // device time of the world-kernel launches (CUDA events)
     int launches = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    DBuf ctl, cd, dtasks, defer, lists;
 
-    Runner(imin_ctx *c, const imin_graph *gr) : ctx(c), g(gr)
+    explicit Runner(imin_ctx *c) : ctx(c)
     {
-        acc.ensure(ctx, 64);
-        claim.ensure(ctx, 16);
-        ndef.ensure(ctx, 16);
-        err.ensure(ctx, 16);
         IM_CUDA(cudaEventCreate(&ev0));
         IM_CUDA(cudaEventCreate(&ev1));
     }
@@ -200,32 +208,23 @@ struct Runner {
         if (ev1) cudaEventDestroy(ev1);
     }
 
-    void timed_launch(const QueryDev &qd, uint32_t flags, uint64_t first, uint32_t count,
-                      const uint32_t *list, const SlotCfg &cfg, void *base, const WorldOut &out)
-    {
-        IM_CUDA(cudaEventRecord(ev0, ctx->stream));
-        launch_worlds(ctx, g, qd, flags, first, count, list, cfg, base, out, claim.as<uint32_t>());
-        IM_CUDA(cudaEventRecord(ev1, ctx->stream));
-        IM_CUDA(cudaEventSynchronize(ev1));
-        float ms = 0.0f;
-        IM_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-        kernel_ms += ms;
-        ++launches;
-    }
-
-    SlotCfg cfg_for(uint32_t flags, int32_t nS, bool big) const
+    SlotCfg cfg_for(uint32_t flags, int32_t n, int64_t m, int32_t nS, bool big) const
     {
         SlotCfg c;
         c.lower = (flags & WF_LOWER) != 0;
         c.upper = (flags & WF_UPPER) != 0;
-        c.bm_words = ((size_t)g->n + 31) / 32;
-        const int32_t n = g->n;
+        c.bm_words = ((size_t)n + 31) / 32;
+        c.groups_per_lane = 2;
+        if (const char *env = std::getenv("IMIN_GROUPS_PER_LANE")) {
+            const long v = std::strtol(env, nullptr, 10);
+            if (v == 1 || v == 2 || v == 4) c.groups_per_lane = (int)v;
+        }
         if (big) {
             c.qcap = n + 1;
-            c.ecap = (int32_t)std::min<int64_t>(std::max<int64_t>(g->m, 1), (int64_t)1 << 28);
-            c.warps = 64;
+            c.ecap = (int32_t)std::min<int64_t>(std::max<int64_t>(m, 1), 4 * ((int64_t)n + 1));
+            c.warps = 256;
         } else {
-            int32_t q = c.lower ? (1 << 17) : (1 << 18);
+            int32_t q = c.lower ? (1 << 19) : (1 << 18);
             // test hook: IMIN_SLOT_QCAP shrinks the per-warp queue so that the
             // deferred-world path (large slots) is exercised on small graphs
             if (const char *env = std::getenv("IMIN_SLOT_QCAP")) {
@@ -233,79 +232,32 @@ struct Runner {
                 if (v > 0 && v < q) q = (int32_t)v;
             }
             c.qcap = std::min<int32_t>(n + 1, std::max<int32_t>(q, nS + 1));
-            c.ecap = c.lower ? std::min<int64_t>(std::max<int64_t>(g->m, 1), 2 * (int64_t)c.qcap) : 0;
+            c.ecap = c.lower ? (int32_t)std::min<int64_t>(std::max<int64_t>(m, 1), 2 * (int64_t)c.qcap) : 0;
             int per_sm = c.lower ? 8 : 32;
             // tuning hook: IMIN_SLOT_WARPS_PER_SM overrides the resident warps per SM
             if (const char *env = std::getenv("IMIN_SLOT_WARPS_PER_SM")) {
                 const long v = std::strtol(env, nullptr, 10);
                 if (v >= 1 && v <= 64) per_sm = (int)v;
             }
+            // never more warps than can be resident at once (the kernel is persistent)
+            per_sm = std::min(per_sm, 8 * world_kernel_blocks_per_sm(flags, c.groups_per_lane));
             c.warps = ctx->num_sms * per_sm;
         }
         // never use more than half of the free device memory for slots
         size_t freeb = 0, totalb = 0;
         cudaMemGetInfo(&freeb, &totalb);
         size_t avail = freeb / 2;
-        if (ctx->budget) avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
+        if (ctx->budget)
+            avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
         const size_t per = c.bytes_per_slot();
         size_t maxw = per ? avail / per : 0;
         maxw = maxw / 8 * 8;
         if ((size_t)c.warps > maxw) c.warps = (int)maxw;
         if (c.warps < 8) {
-            // fall back to one block of 8 slots if anything fits at all
             if (per * 8 > freeb) fail(IMIN_ENOMEM, "not enough device memory for sampling slots");
             c.warps = 8;
         }
         return c;
-    }
-
-    void reset_acc()
-    {
-        IM_CUDA(cudaMemsetAsync(acc.p, 0, 64, ctx->stream));
-        IM_CUDA(cudaMemsetAsync(err.p, 0, 16, ctx->stream));
-    }
-
-    // Runs worlds [first, first + count).  Worlds that overflow a per-warp buffer
-    // or the store are re-run on large slots after `grow` (which may enlarge the
-    // store and must update `out`) until none is left.
-    template <class Grow>
-    void run(const QueryDev &qd, uint32_t flags, uint64_t first, uint32_t count, WorldOut &out,
-             Grow grow)
-    {
-        claimed_main = 0;
-        if (count == 0) return;
-        out.acc = acc.as<unsigned long long>();
-        out.err = err.as<uint32_t>();
-        deferred.ensure(ctx, (size_t)count * 4 + 16);
-        out.deferred = deferred.as<uint32_t>();
-        out.deferred_cap = count;
-        out.n_deferred = ndef.as<uint32_t>();
-        IM_CUDA(cudaMemsetAsync(ndef.p, 0, 4, ctx->stream));
-        SlotCfg cfg = cfg_for(flags, qd.nS, false);
-        prepare_slots(ctx->slots, cfg, ctx->slots_layout);
-        timed_launch(qd, flags, first, count, nullptr, cfg, ctx->slots.p, out);
-        uint32_t nd = 0, cl = 0;
-        IM_CUDA(cudaMemcpyAsync(&nd, ndef.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
-        IM_CUDA(cudaMemcpyAsync(&cl, claim.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
-        IM_CUDA(cudaStreamSynchronize(ctx->stream));
-        claimed_main = std::min<uint32_t>(cl, count);
-        check_err();
-        int rounds = 0;
-        DBuf list;
-        while (nd > 0) {
-            if (++rounds > 40) fail(IMIN_ERANGE, "worlds could not be stored after repeated growth");
-            grow(nd);
-            list.ensure(ctx, (size_t)nd * 4);
-            IM_CUDA(cudaMemcpyAsync(list.p, deferred.p, (size_t)nd * 4, cudaMemcpyDeviceToDevice,
-                                    ctx->stream));
-            IM_CUDA(cudaMemsetAsync(ndef.p, 0, 4, ctx->stream));
-            SlotCfg big = cfg_for(flags, qd.nS, true);
-            prepare_slots(ctx->big_slots, big, ctx->big_slots_layout);
-            timed_launch(qd, flags, first, nd, list.as<uint32_t>(), big, ctx->big_slots.p, out);
-            IM_CUDA(cudaMemcpyAsync(&nd, ndef.p, 4, cudaMemcpyDeviceToHost, ctx->stream));
-            IM_CUDA(cudaStreamSynchronize(ctx->stream));
-            check_err();
-        }
     }
 
     // Slot bitmaps must start clear; the kernel leaves them clear after every world,
@@ -315,30 +267,142 @@ struct Runner {
         const size_t bytes = cfg.bytes_per_slot() * (size_t)cfg.warps;
         const size_t key = cfg.bytes_per_slot() * 1315423911u + (size_t)cfg.warps;
         const void *before = arena.p;
-        arena.ensure(ctx, bytes);
+        if (arena.p && arena.bytes < bytes) arena.release();   // never hold two arenas at once
+        arena.ensure(ctx, bytes, false, true);
         if (arena.p != before || layout != key) {
             IM_CUDA(cudaMemsetAsync(arena.p, 0, arena.bytes, ctx->stream));
             layout = key;
         }
     }
 
-    void check_err()
+    void launch(const std::vector<WTask> &ht, const imin_graph *g0, uint32_t flags,
+                const SlotCfg &cfg, DBuf &arena)
     {
-        uint32_t e = 0;
-        IM_CUDA(cudaMemcpy(&e, err.p, 4, cudaMemcpyDeviceToHost));
-        if (e & DERR_TIMEOUT) fail(IMIN_ETIMEOUT, "a bounded device loop gave up");
-        if (e & DERR_INTERNAL) fail(IMIN_EDEVICE, "device invariant failed");
+        const int n = (int)ht.size();
+        dtasks.ensure(ctx, ht.size() * sizeof(WTask));
+        cd.ensure(ctx, (size_t)n * 8 + 16);
+        IM_CUDA(cudaMemcpyAsync(dtasks.p, ht.data(), ht.size() * sizeof(WTask), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)n * 8, ctx->stream));
+        IM_CUDA(cudaEventRecord(ev0, ctx->stream));
+        launch_tasks(ctx, dtasks.as<WTask>(), n, g0, flags, cfg, arena.p, cd.as<uint32_t>(),
+                     cd.as<uint32_t>() + n);
+        IM_CUDA(cudaEventRecord(ev1, ctx->stream));
+        IM_CUDA(cudaEventSynchronize(ev1));
+        float ms = 0.0f;
+        IM_CUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+        kernel_ms += ms;
+        ++launches;
     }
 
-    void read_acc()
+    void run(std::vector<TaskRun *> &T, uint32_t flags)
     {
-        IM_CUDA(cudaMemcpyAsync(h_acc, acc.p, 64, cudaMemcpyDeviceToHost, ctx->stream));
-        IM_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int n = (int)T.size();
+        if (n == 0) return;
+        ctl.ensure(ctx, (size_t)n * CTL);
+        IM_CUDA(cudaMemsetAsync(ctl.p, 0, (size_t)n * CTL, ctx->stream));
+        std::vector<size_t> doff(n + 1, 0);
+        int32_t nmax = 1, nSmax = 1;
+        int64_t mmax = 1;
+        for (int i = 0; i < n; ++i) {
+            doff[i + 1] = doff[i] + T[i]->count;
+            nmax = std::max(nmax, T[i]->g->n);
+            mmax = std::max(mmax, T[i]->g->m);
+            nSmax = std::max(nSmax, T[i]->q.nS);
+        }
+        defer.ensure(ctx, doff[n] * 4 + 16);
+        char *c0 = reinterpret_cast<char *>(ctl.p);
+        for (int i = 0; i < n; ++i) {
+            WorldOut &o = T[i]->out;
+            o.acc = reinterpret_cast<unsigned long long *>(c0 + (size_t)i * CTL);
+            o.n_deferred = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 64);
+            o.err = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 68);
+            o.deferred = defer.as<uint32_t>() + doff[i];
+            o.deferred_cap = T[i]->count;
+        }
+        SlotCfg cfg = cfg_for(flags, nmax, mmax, nSmax, false);
+        DBuf &arena = cfg.lower ? ctx->slots_lower : ctx->slots;
+        size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
+        prepare_slots(arena, cfg, layout);
+        std::vector<WTask> ht;
+        for (int i = 0; i < n; ++i)
+            ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, nullptr, T[i]->out));
+        launch(ht, T[0]->g, flags, cfg, arena);
+        std::vector<unsigned char> hc((size_t)n * CTL);
+        std::vector<uint32_t> claims(n);
+        IM_CUDA(cudaMemcpy(claims.data(), cd.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n; ++i) T[i]->claimed_main = std::min(claims[i], T[i]->count);
+        check_err(hc, n);
+        std::vector<uint32_t> h_def;
+        for (int rounds = 0;; ++rounds) {
+            std::vector<uint32_t> nd(n);
+            bool any = false;
+            for (int i = 0; i < n; ++i) {
+                std::memcpy(&nd[i], hc.data() + (size_t)i * CTL + 64, 4);
+                any |= nd[i] > 0;
+            }
+            if (!any) break;
+            if (rounds > 40) fail(IMIN_ERANGE, "worlds could not be stored after repeated growth");
+            // worlds flagged in the top bit overflowed their slot and need a large slot;
+            // the others only lacked store room and re-run on normal slots
+            std::vector<std::vector<uint32_t>> small(n), big(n);
+            for (int i = 0; i < n; ++i) {
+                if (!nd[i]) continue;
+                if (T[i]->grow) T[i]->grow(nd[i]);
+                h_def.resize(nd[i]);
+                IM_CUDA(cudaMemcpy(h_def.data(), defer.as<uint32_t>() + doff[i], (size_t)nd[i] * 4,
+                                   cudaMemcpyDeviceToHost));
+                for (uint32_t x : h_def)
+                    ((x & 0x80000000u) ? big[i] : small[i]).push_back(x & 0x7fffffffu);
+                IM_CUDA(cudaMemsetAsync(c0 + (size_t)i * CTL + 64, 0, 4, ctx->stream));
+            }
+            for (int pass = 0; pass < 2; ++pass) {
+                std::vector<std::vector<uint32_t>> &L = pass == 0 ? small : big;
+                size_t tot = 0;
+                for (int i = 0; i < n; ++i) tot += L[i].size();
+                if (!tot) continue;
+                lists.ensure(ctx, tot * 4);
+                std::vector<WTask> lt;
+                size_t at = 0;
+                for (int i = 0; i < n; ++i) {
+                    if (L[i].empty()) continue;
+                    IM_CUDA(cudaMemcpy(lists.as<uint32_t>() + at, L[i].data(), L[i].size() * 4,
+                                       cudaMemcpyHostToDevice));
+                    lt.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, (uint32_t)L[i].size(),
+                                           lists.as<uint32_t>() + at, T[i]->out));
+                    at += L[i].size();
+                }
+                if (pass == 0) {
+                    launch(lt, T[0]->g, flags, cfg, arena);
+                } else {
+                    SlotCfg bc = cfg_for(flags, nmax, mmax, nSmax, true);
+                    prepare_slots(ctx->big_slots, bc, ctx->big_slots_layout);
+                    launch(lt, T[0]->g, flags, bc, ctx->big_slots);
+                }
+            }
+            IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));
+            check_err(hc, n);
+        }
+        for (int i = 0; i < n; ++i) std::memcpy(T[i]->acc, hc.data() + (size_t)i * CTL, 64);
+    }
+
+    void check_err(const std::vector<unsigned char> &hc, int n)
+    {
+        uint32_t e = 0;
+        for (int i = 0; i < n; ++i) {
+            uint32_t x;
+            std::memcpy(&x, hc.data() + (size_t)i * CTL + 68, 4);
+            e |= x;
+        }
+        if (e & DERR_TIMEOUT) fail(IMIN_ETIMEOUT, "a bounded device loop gave up");
+        if (e & DERR_INTERNAL) fail(IMIN_EDEVICE, "device invariant failed");
     }
 };
 
 // ---------------------------------------------------------------------------
-// Stopping-rule spread estimate (reach-only worlds with early exit)
+// Stopping-rule spread estimates (reach-only worlds with early exit), several
+// queries in one launch
 // ---------------------------------------------------------------------------
 struct SpreadEst {
     double I = 0.0;
@@ -347,56 +411,83 @@ struct SpreadEst {
     double kernel_ms = 0.0;
 };
 
+struct StopSpec {
+    const imin_graph *g;
+    const Query *q;
+    double beta, dprime;
+    uint64_t key;
+    uint32_t tag, inst;
+    SpreadEst est;
+};
+
+void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
+{
+    const size_t ns = specs.size();
+    std::vector<TaskRun> tr(ns);
+    std::vector<TaskRun *> tp;
+    std::vector<DBuf> spread(ns);
+    std::vector<double> W(ns), ups1(ns);
+    std::vector<unsigned long long> T(ns);
+    for (size_t i = 0; i < ns; ++i) {
+        StopSpec &sp = specs[i];
+        W[i] = (double)sp.q->Vs.size() + (double)sp.q->S.size();
+        const double ups = 4.0 * (IM_E - 2.0) * std::log(2.0 / sp.dprime) / (sp.beta * sp.beta);
+        ups1[i] = 1.0 + (1.0 + sp.beta) * ups;
+        const double Td = std::ceil(ups1[i] * W[i]);
+        if (!(Td < 1.8e19)) fail(IMIN_ERANGE, "stopping threshold too large");
+        T[i] = (unsigned long long)Td;
+        // every world reaches at least |S| nodes, so N <= ceil(T / |S|)
+        const uint64_t nmax = (T[i] + sp.q->S.size() - 1) / sp.q->S.size();
+        if (nmax >= ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "the stopping rule may need >= 2^31 worlds");
+        spread[i].ensure(ctx, (size_t)nmax * 4 + 16);
+        tr[i].g = sp.g;
+        tr[i].q = qdev(*sp.q, sp.key, sp.tag, sp.inst);
+        tr[i].first = 0;
+        tr[i].count = (uint32_t)nmax;
+        tr[i].out.world_spread = spread[i].as<uint32_t>();
+        tr[i].out.stop_T = T[i];
+        tp.push_back(&tr[i]);
+    }
+    Runner run(ctx);
+    run.run(tp, WF_STOP | WF_SPREAD);
+    for (size_t i = 0; i < ns; ++i) {
+        // every claimed world is complete (deferred ones were re-run), and the worlds
+        // below the last claimed index hold at least T reached nodes in total
+        const uint64_t want = tr[i].claimed_main;
+        std::vector<uint32_t> sizes(want);
+        if (want) IM_CUDA(cudaMemcpy(sizes.data(), spread[i].p, want * 4, cudaMemcpyDeviceToHost));
+        unsigned long long sum = 0;
+        uint64_t N = 0;
+        for (uint64_t j = 0; j < want; ++j) {
+            sum += sizes[j];
+            if (sum >= T[i]) {
+                N = j + 1;
+                break;
+            }
+        }
+        if (N == 0) fail(IMIN_EDEVICE, "stopping rule: threshold not reached by the traversed worlds");
+        SpreadEst &r = specs[i].est;
+        r.N = N;
+        r.I = W[i] * ups1[i] / (double)N;
+        r.worlds = tr[i].acc[4];
+        r.edges = tr[i].acc[1];
+        r.nodes = tr[i].acc[0];
+    }
+    // device time is shared by the tasks of the launch: report it on the first
+    specs[0].est.kernel_ms = run.kernel_ms;
+    specs[0].est.launches = (uint64_t)run.launches;
+}
+
 SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double beta, double dprime,
                     uint64_t key, uint32_t tag, uint32_t inst)
 {
-    const double W = (double)q.Vs.size() + (double)q.S.size();
-    const double ups = 4.0 * (IM_E - 2.0) * std::log(2.0 / dprime) / (beta * beta);
-    const double ups1 = 1.0 + (1.0 + beta) * ups;
-    const double Td = std::ceil(ups1 * W);
-    if (!(Td < 1.8e19)) fail(IMIN_ERANGE, "stopping threshold too large");
-    const unsigned long long T = (unsigned long long)Td;
-    // every world reaches at least |S| nodes, so N <= ceil(T / |S|)
-    const uint64_t nmax = (T + q.S.size() - 1) / q.S.size();
-    if (nmax >= ((uint64_t)1 << 32)) fail(IMIN_ERANGE, "the stopping rule may need >= 2^32 worlds");
-    Runner run(ctx, g);
-    run.reset_acc();
-    DBuf spread;
-    spread.ensure(ctx, (size_t)nmax * 4 + 16);
-    QueryDev qd = qdev(q, key, tag, inst);
-    WorldOut out;
-    out.world_spread = spread.as<uint32_t>();
-    out.stop_T = T;
-    run.run(qd, WF_STOP | WF_SPREAD, 0, (uint32_t)nmax, out, [](uint32_t) {});
-    // every claimed world is complete (deferred ones were re-run), and the worlds
-    // below the last claimed index hold at least T reached nodes in total
-    run.read_acc();
-    const uint64_t want = run.claimed_main;
-    std::vector<uint32_t> sizes(want);
-    if (want) IM_CUDA(cudaMemcpy(sizes.data(), spread.p, want * 4, cudaMemcpyDeviceToHost));
-    unsigned long long sum = 0;
-    uint64_t N = 0;
-    for (uint64_t j = 0; j < want; ++j) {
-        sum += sizes[j];
-        if (sum >= T) {
-            N = j + 1;
-            break;
-        }
-    }
-    if (N == 0) fail(IMIN_EDEVICE, "stopping rule: threshold not reached by the traversed worlds");
-    SpreadEst r;
-    r.N = N;
-    r.I = W * ups1 / (double)N;
-    r.worlds = run.h_acc[4];
-    r.edges = run.h_acc[1];
-    r.nodes = run.h_acc[0];
-    r.kernel_ms = run.kernel_ms;
-    r.launches = (uint64_t)run.launches;
-    return r;
+    std::vector<StopSpec> v{StopSpec{g, &q, beta, dprime, key, tag, inst, SpreadEst{}}};
+    stop_rules(ctx, v);
+    return v[0].est;
 }
 
 // ---------------------------------------------------------------------------
-// Collections
+// Collections: CP records (C1, C2) and LRR sets (L1, L2), appended together
 // ---------------------------------------------------------------------------
 void cp_reserve(imin_ctx *ctx, CpStore &c, unsigned long long need)
 {
@@ -409,52 +500,77 @@ void cp_reserve(imin_ctx *ctx, CpStore &c, unsigned long long need)
     c.cap = cap;
 }
 
-// append worlds [from, to) of tag to a CP collection (credit optional)
-void sample_cp(imin_ctx *ctx, const imin_graph *g, const Query &q, CpStore &c, uint64_t from,
-               uint64_t to, uint64_t key, uint32_t tag, uint32_t inst, double est_per_world,
-               unsigned long long *credit, SpreadEst *stats)
+struct CpJob {
+    CpStore *c;
+    uint32_t tag;
+    unsigned long long *credit;   // may be null
+};
+
+// append worlds [from, to) of each job's tag to its CP collection, one launch for all jobs
+void sample_cp(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<CpJob> &jobs,
+               uint64_t from, uint64_t to, uint64_t key, uint32_t inst, double est_per_world,
+               SpreadEst *stats)
 {
     if (to <= from) return;
-    if (to > ((uint64_t)1 << 32)) fail(IMIN_ERANGE, "world index >= 2^32");
-    c.cursor.ensure(ctx, 16);
-    if (c.worlds == 0) {
-        IM_CUDA(cudaMemsetAsync(c.cursor.p, 0, 8, ctx->stream));
-        c.count = 0;
+    if (to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
+    const size_t nj = jobs.size();
+    std::vector<TaskRun> tr(nj);
+    std::vector<TaskRun *> tp;
+    std::vector<unsigned long long> before(nj);
+    for (size_t i = 0; i < nj; ++i) {
+        CpStore &c = *jobs[i].c;
+        c.cursor.ensure(ctx, 16);
+        if (c.worlds == 0) {
+            IM_CUDA(cudaMemsetAsync(c.cursor.p, 0, 8, ctx->stream));
+            c.count = 0;
+        }
+        const unsigned long long est =
+            (unsigned long long)((double)(to - from) * std::max(est_per_world, 1.0) * 1.25) + 4096;
+        cp_reserve(ctx, c, (unsigned long long)c.count + est);
+        before[i] = (unsigned long long)c.count;
+        TaskRun &t = tr[i];
+        t.g = g;
+        t.q = qdev(q, key, jobs[i].tag, inst);
+        t.first = from;
+        t.count = (uint32_t)(to - from);
+        t.out.credit_L = jobs[i].credit;
+        t.out.rec_node = c.node.as<int32_t>();
+        t.out.rec_par = c.par.as<int32_t>();
+        t.out.rec_size = c.size.as<int32_t>();
+        t.out.rec_cursor = c.cursor.as<unsigned long long>();
+        t.out.rec_cap = c.cap;
+        CpStore *cp = &c;
+        TaskRun *self = &t;
+        const unsigned long long b0 = before[i];
+        t.grow = [ctx, cp, self, b0, from, to, g](uint32_t nd) {
+            unsigned long long used = 0;
+            IM_CUDA(cudaMemcpy(&used, cp->cursor.p, 8, cudaMemcpyDeviceToHost));
+            const uint64_t worlds = (to - from) > nd ? (to - from) - nd : 1;
+            const unsigned long long avg = (used - b0) / worlds + 1;
+            cp_reserve(ctx, *cp, std::max<unsigned long long>(
+                                     2 * cp->cap, used + (unsigned long long)nd * 2 * avg + (unsigned long long)g->n));
+            self->out.rec_node = cp->node.as<int32_t>();
+            self->out.rec_par = cp->par.as<int32_t>();
+            self->out.rec_size = cp->size.as<int32_t>();
+            self->out.rec_cap = cp->cap;
+        };
+        tp.push_back(&t);
     }
-    const unsigned long long est =
-        (unsigned long long)((double)(to - from) * std::max(est_per_world, 1.0) * 1.25) + 4096;
-    cp_reserve(ctx, c, (unsigned long long)c.count + est);
-    Runner run(ctx, g);
-    run.reset_acc();
-    QueryDev qd = qdev(q, key, tag, inst);
-    WorldOut out;
-    out.credit_L = credit;
-    out.rec_node = c.node.as<int32_t>();
-    out.rec_par = c.par.as<int32_t>();
-    out.rec_size = c.size.as<int32_t>();
-    out.rec_cursor = c.cursor.as<unsigned long long>();
-    out.rec_cap = c.cap;
-    const unsigned long long before = (unsigned long long)c.count;
-    run.run(qd, WF_LOWER | WF_STORE, from, (uint32_t)(to - from), out, [&](uint32_t nd) {
+    Runner run(ctx);
+    run.run(tp, WF_LOWER | WF_STORE);
+    for (size_t i = 0; i < nj; ++i) {
+        CpStore &c = *jobs[i].c;
         unsigned long long used = 0;
         IM_CUDA(cudaMemcpy(&used, c.cursor.p, 8, cudaMemcpyDeviceToHost));
-        const uint64_t worlds = (to - from) > nd ? (to - from) - nd : 1;
-        const unsigned long long avg = (used - before) / worlds + 1;
-        cp_reserve(ctx, c, std::max<unsigned long long>(2 * c.cap, used + (unsigned long long)nd * 2 * avg + (unsigned long long)g->n));
-        out.rec_node = c.node.as<int32_t>();
-        out.rec_par = c.par.as<int32_t>();
-        out.rec_size = c.size.as<int32_t>();
-        out.rec_cap = c.cap;
-    });
-    unsigned long long used = 0;
-    IM_CUDA(cudaMemcpy(&used, c.cursor.p, 8, cudaMemcpyDeviceToHost));
-    c.count = (long long)used;
-    c.worlds += to - from;
-    run.read_acc();
+        c.count = (long long)used;
+        c.worlds += to - from;
+        if (stats) {
+            stats->worlds += tr[i].acc[4];
+            stats->edges += tr[i].acc[1];
+            stats->nodes += tr[i].acc[0];
+        }
+    }
     if (stats) {
-        stats->worlds += run.h_acc[4];
-        stats->edges += run.h_acc[1];
-        stats->nodes += run.h_acc[0];
         stats->kernel_ms += run.kernel_ms;
         stats->launches += (uint64_t)run.launches;
     }
@@ -477,46 +593,70 @@ void lrr_reserve(imin_ctx *ctx, LrrStore &L, unsigned long long need_elems, uint
     }
 }
 
-void sample_lrr(imin_ctx *ctx, const imin_graph *g, const Query &q, LrrStore &L, uint64_t from,
-                uint64_t to, uint64_t key, uint32_t tag, uint32_t inst,
-                unsigned long long *credit, SpreadEst *stats)
+struct LrrJob {
+    LrrStore *L;
+    uint32_t tag;
+    unsigned long long *credit;   // may be null
+};
+
+void sample_lrr(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<LrrJob> &jobs,
+                uint64_t from, uint64_t to, uint64_t key, uint32_t inst, SpreadEst *stats)
 {
     if (to <= from) return;
-    if (to > ((uint64_t)1 << 32)) fail(IMIN_ERANGE, "world index >= 2^32");
-    L.cursor.ensure(ctx, 16);
-    if (L.nsets == 0) {
-        IM_CUDA(cudaMemsetAsync(L.cursor.p, 0, 8, ctx->stream));
-        L.elems = 0;
+    if (to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
+    const size_t nj = jobs.size();
+    std::vector<TaskRun> tr(nj);
+    std::vector<TaskRun *> tp;
+    for (size_t i = 0; i < nj; ++i) {
+        LrrStore &L = *jobs[i].L;
+        L.cursor.ensure(ctx, 16);
+        if (L.nsets == 0) {
+            IM_CUDA(cudaMemsetAsync(L.cursor.p, 0, 8, ctx->stream));
+            L.elems = 0;
+        }
+        // start from the average set size seen so far (64 per world before any is known)
+        const unsigned long long per = L.nsets ? L.elems / L.nsets + 1 : 64;
+        lrr_reserve(ctx, L, L.elems + (to - from) * per * 2 + 65536, to);
+        TaskRun &t = tr[i];
+        t.g = g;
+        t.q = qdev(q, key, jobs[i].tag, inst);
+        t.first = from;
+        t.count = (uint32_t)(to - from);
+        t.out.credit_U = jobs[i].credit;
+        t.out.set_elem = L.elem.as<int32_t>();
+        t.out.set_off = L.off.as<unsigned long long>() + from;
+        t.out.set_len = L.len.as<uint32_t>() + from;
+        t.out.set_cursor = L.cursor.as<unsigned long long>();
+        t.out.set_cap = L.cap;
+        LrrStore *lp = &L;
+        TaskRun *self = &t;
+        t.grow = [ctx, lp, self, from, to, g](uint32_t nd) {
+            unsigned long long used = 0;
+            IM_CUDA(cudaMemcpy(&used, lp->cursor.p, 8, cudaMemcpyDeviceToHost));
+            lrr_reserve(ctx, *lp, std::max<unsigned long long>(
+                                      2 * lp->cap, used + (unsigned long long)nd * (unsigned long long)g->n), to);
+            self->out.set_elem = lp->elem.as<int32_t>();
+            self->out.set_off = lp->off.as<unsigned long long>() + from;
+            self->out.set_len = lp->len.as<uint32_t>() + from;
+            self->out.set_cap = lp->cap;
+        };
+        tp.push_back(&t);
     }
-    lrr_reserve(ctx, L, L.elems + (to - from) * 8 + 4096, to);
-    Runner run(ctx, g);
-    run.reset_acc();
-    QueryDev qd = qdev(q, key, tag, inst);
-    WorldOut out;
-    out.credit_U = credit;
-    out.set_elem = L.elem.as<int32_t>();
-    out.set_off = L.off.as<unsigned long long>() + from;
-    out.set_len = L.len.as<uint32_t>() + from;
-    out.set_cursor = L.cursor.as<unsigned long long>();
-    out.set_cap = L.cap;
-    run.run(qd, WF_UPPER | WF_STORE, from, (uint32_t)(to - from), out, [&](uint32_t nd) {
+    Runner run(ctx);
+    run.run(tp, WF_UPPER | WF_STORE);
+    for (size_t i = 0; i < nj; ++i) {
+        LrrStore &L = *jobs[i].L;
         unsigned long long used = 0;
         IM_CUDA(cudaMemcpy(&used, L.cursor.p, 8, cudaMemcpyDeviceToHost));
-        lrr_reserve(ctx, L, std::max<unsigned long long>(2 * L.cap, used + (unsigned long long)nd * (unsigned long long)g->n), to);
-        out.set_elem = L.elem.as<int32_t>();
-        out.set_off = L.off.as<unsigned long long>() + from;
-        out.set_len = L.len.as<uint32_t>() + from;
-        out.set_cap = L.cap;
-    });
-    unsigned long long used = 0;
-    IM_CUDA(cudaMemcpy(&used, L.cursor.p, 8, cudaMemcpyDeviceToHost));
-    L.elems = used;
-    L.nsets = (uint32_t)to;
-    run.read_acc();
+        L.elems = used;
+        L.nsets = (uint32_t)to;
+        if (stats) {
+            stats->worlds += tr[i].acc[4];
+            stats->edges += tr[i].acc[1];
+            stats->nodes += tr[i].acc[0];
+        }
+    }
     if (stats) {
-        stats->worlds += run.h_acc[4];
-        stats->edges += run.h_acc[1];
-        stats->nodes += run.h_acc[0];
         stats->kernel_ms += run.kernel_ms;
         stats->launches += (uint64_t)run.launches;
     }
@@ -661,7 +801,13 @@ void imin_destroy(imin_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->persist_set) {
+        cudaCtxResetPersistingL2Cache();
+        cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->prev_persist_limit);
+        cudaGetLastError();
+    }
     ctx->slots.release();
+    ctx->slots_lower.release();
     ctx->big_slots.release();
     ctx->misc.release();
     delete ctx;
@@ -728,8 +874,8 @@ int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *bloc
         if (opts->reserved != 0 || (mode & ~(uint32_t)(IMIN_REACH | IMIN_CREDIT_LOWER |
                                                        IMIN_CREDIT_UPPER | IMIN_OUT_DEVICE)))
             fail(IMIN_EINVAL, "unknown mode bits");
-        if (opts->first_sample + theta > ((uint64_t)1 << 32) || theta >= ((uint64_t)1 << 32))
-            fail(IMIN_ERANGE, "world index >= 2^32");
+        if (opts->first_sample + theta > ((uint64_t)1 << 32) || theta >= ((uint64_t)1 << 31))
+            fail(IMIN_ERANGE, "world index >= 2^32 or theta >= 2^31");
         Query q;
         const bool upper = (mode & IMIN_CREDIT_UPPER) != 0, lower = (mode & IMIN_CREDIT_LOWER) != 0;
         prepare_query(ctx, g, q, S, nS, blocked, nB, upper);
@@ -762,21 +908,25 @@ int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *bloc
                 pws = dws.as<uint32_t>();
             }
         }
-        Runner run(ctx, g);
-        run.reset_acc();
-        QueryDev qd = qdev(q, opts->key, opts->tag, opts->inst);
-        WorldOut wo;
-        wo.reach = preach;
-        wo.credit_L = pcl;
-        wo.credit_U = pcu;
-        wo.world_spread = pws;
+        TaskRun t;
+        t.g = g;
+        t.q = qdev(q, opts->key, opts->tag, opts->inst);
+        t.first = opts->first_sample;
+        t.count = (uint32_t)theta;
+        t.out.reach = preach;
+        t.out.credit_L = pcl;
+        t.out.credit_U = pcu;
+        t.out.world_spread = pws;
         uint32_t flags = (preach ? WF_REACH : 0u) | (lower ? WF_LOWER : 0u) | (upper ? WF_UPPER : 0u) |
                          (pws ? WF_SPREAD : 0u);
-        run.run(qd, flags, opts->first_sample, (uint32_t)theta, wo, [](uint32_t) {});
-        run.read_acc();
-        out->total_spread = run.h_acc[0];
-        out->edges_scanned = run.h_acc[1];
-        out->nonempty_lrr = run.h_acc[2];
+        if (theta > 0) {
+            std::vector<TaskRun *> tp{&t};
+            Runner run(ctx);
+            run.run(tp, flags);
+        }
+        out->total_spread = t.acc[0];
+        out->edges_scanned = t.acc[1];
+        out->nonempty_lrr = t.acc[2];
         if (!dev_out) {
             if (preach) IM_CUDA(cudaMemcpyAsync(out->reach, preach, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
             if (pcl) IM_CUDA(cudaMemcpyAsync(out->credit_lower, pcl, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
@@ -917,8 +1067,9 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
             IM_CUDA(cudaMemsetAsync(credC1.p, 0, (size_t)n * 8, ctx->stream));
             const double per_world = std::max(I_hat - (double)nS, 1.0);
             SpreadEst st;
-            sample_cp(ctx, g, q, C1, 0, th, key, 1, inst, per_world, credC1.as<unsigned long long>(), &st);
-            sample_cp(ctx, g, q, C2, 0, th, key, 2, inst, per_world, nullptr, &st);
+            std::vector<CpJob> cj{CpJob{&C1, 1u, credC1.as<unsigned long long>()},
+                                  CpJob{&C2, 2u, nullptr}};
+            sample_cp(ctx, g, q, cj, 0, th, key, inst, per_world, &st);
             double samp_ms = ts.ms(), greedy_ms = 0.0;
             GreedyOut go;
             double sL = 0.0, sU = 0.0;
@@ -945,8 +1096,7 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
                 res->iters_L = i;
                 if (sL / sU >= one_m_inv_e_m_eps || i == imax) break;
                 Timer ts2;
-                sample_cp(ctx, g, q, C1, th, 2 * th, key, 1, inst, per_world, credC1.as<unsigned long long>(), &st);
-                sample_cp(ctx, g, q, C2, th, 2 * th, key, 2, inst, per_world, nullptr, &st);
+                sample_cp(ctx, g, q, cj, th, 2 * th, key, inst, per_world, &st);
                 samp_ms += ts2.ms();
                 th *= 2;
             }
@@ -991,8 +1141,9 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
             credL1.ensure(ctx, (size_t)n * 8);
             IM_CUDA(cudaMemsetAsync(credL1.p, 0, (size_t)n * 8, ctx->stream));
             SpreadEst st;
-            sample_lrr(ctx, g, q, L1, 0, th, key, 3, inst, credL1.as<unsigned long long>(), &st);
-            sample_lrr(ctx, g, q, L2, 0, th, key, 4, inst, nullptr, &st);
+            std::vector<LrrJob> lj{LrrJob{&L1, 3u, credL1.as<unsigned long long>()},
+                                   LrrJob{&L2, 4u, nullptr}};
+            sample_lrr(ctx, g, q, lj, 0, th, key, inst, &st);
             double samp_ms = ts.ms(), greedy_ms = 0.0;
             GreedyOut go;
             double sL = 0.0, sU = 0.0;
@@ -1013,8 +1164,7 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
                 res->iters_U = i;
                 if (sL / sU >= one_m_inv_e_m_eps || i == imax) break;
                 Timer ts2;
-                sample_lrr(ctx, g, q, L1, th, 2 * th, key, 3, inst, credL1.as<unsigned long long>(), &st);
-                sample_lrr(ctx, g, q, L2, th, 2 * th, key, 4, inst, nullptr, &st);
+                sample_lrr(ctx, g, q, lj, th, 2 * th, key, inst, &st);
                 samp_ms += ts2.ms();
                 th *= 2;
             }
@@ -1040,14 +1190,22 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
         Timer tf;
         const std::vector<int32_t> *cand[3] = {&BLv, &BUv, &BRv};
         const bool use[3] = {do_L, do_U, do_R};
-        int best = -1;
+        Query qb[3];
+        std::vector<StopSpec> fin;
+        std::vector<int> fin_c;
         for (int c = 0; c < 3; ++c) {
             res->I_after[c] = 0.0;
             if (!use[c]) continue;
-            Query qb;
-            prepare_query(ctx, g, qb, S.data(), (int32_t)S.size(), cand[c]->data(),
+            prepare_query(ctx, g, qb[c], S.data(), (int32_t)S.size(), cand[c]->data(),
                           (int32_t)cand[c]->size(), true);
-            SpreadEst e = stop_rule(ctx, g, qb, gamma, delta, key, (uint32_t)(5 + c), inst);
+            fin.push_back(StopSpec{g, &qb[c], gamma, delta, key, (uint32_t)(5 + c), inst, SpreadEst{}});
+            fin_c.push_back(c);
+        }
+        stop_rules(ctx, fin);
+        int best = -1;
+        for (size_t i = 0; i < fin.size(); ++i) {
+            const int c = fin_c[i];
+            const SpreadEst &e = fin[i].est;
             res->I_after[c] = e.I;
             res->n_final[c] = e.N;
             res->worlds_sampled += e.worlds;
@@ -1056,8 +1214,9 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
             res->reach_nodes += e.nodes;
             res->reach_edges += e.edges;
             res->reach_launches += e.launches;
-            if (best < 0 || e.I < res->I_after[best]) best = c;
         }
+        for (int c = 0; c < 3; ++c)
+            if (use[c] && (best < 0 || res->I_after[c] < res->I_after[best])) best = c;
         res->ms_stage[5] = tf.ms();
         res->chosen = best;
         res->n_blockers = (int32_t)cand[best]->size();

@@ -89,8 +89,9 @@ struct DBuf {
     DBuf &operator=(const DBuf &) = delete;
     ~DBuf() { release(); }
     void release();
-    // ensure capacity (contents are NOT preserved unless keep = true)
-    void ensure(imin_ctx *c, size_t need, bool keep = false);
+    // ensure capacity (contents are NOT preserved unless keep = true); `exact` allocates
+    // exactly `need` bytes instead of growing geometrically
+    void ensure(imin_ctx *c, size_t need, bool keep = false, bool exact = false);
     template <class T> T *as() const { return reinterpret_cast<T *>(p); }
 };
 
@@ -102,9 +103,14 @@ struct imin_ctx {
     int num_sms = 0;
     std::string last_error;
     // scratch shared by calls (grow-only)
-    DBuf slots;             // world-kernel slot arena
+    DBuf slots;             // world-kernel slot arena (reach-only and upper-bound worlds)
+    DBuf slots_lower;       // slot arena of lower-bound worlds (larger slots, fewer of them)
     DBuf big_slots;         // slots for deferred (oversized) worlds
-    size_t slots_layout = 0, big_slots_layout = 0;
+    size_t slots_layout = 0, slots_lower_layout = 0, big_slots_layout = 0;
+    // L2 persistence for the graph's edge array (0 = not available)
+    size_t l2_window_bytes = 0, l2_persist_bytes = 0;
+    size_t prev_persist_limit = 0;
+    bool persist_set = false;
     DBuf misc;              // small per-call device scalars
     DBuf hostpin_dummy;
     unsigned long long *h_misc = nullptr;  // pinned host mirror of `misc` scalars
@@ -122,6 +128,8 @@ struct imin_graph {
     int64_t m = 0, m4 = 0;
     // device
     DBuf row_ptr, col, thr, in_ptr, in_src, in_eid, in_thr;
+    DBuf ce;                // per 4-edge group {col x4, thr x4}: one 32-byte sector per group
+    size_t ce_bytes = 0;
     // host copies used by the controller (ON, q(v), out-degrees, V'_s)
     std::vector<int32_t> h_row_ptr, h_col;
     std::vector<uint32_t> h_thr;
@@ -145,6 +153,7 @@ struct SlotCfg {
     int32_t ecap = 0;       // live-edge pair capacity per slot (lower bound only)
     size_t bm_words = 0;    // 32-bit words of one visited bitmap
     bool lower = false, upper = false;
+    int groups_per_lane = 2;  // U: 4-edge groups each lane has in flight per step
     size_t bytes_per_slot() const;
 };
 
@@ -176,19 +185,39 @@ struct QueryDev {
     int32_t nS = 0;
     const uint32_t *seed_bm = nullptr;
     const uint32_t *blocked_bm = nullptr;   // may be null
+    const int32_t *B = nullptr;      // device, nB blocked nodes (pre-marked in reach-only worlds)
+    int32_t nB = 0;
     const int32_t *Vs = nullptr;     // device, sorted ascending
     int32_t nVs = 0;
     uint64_t key = 0;
     uint32_t tag = 0, inst = 0;
 };
 
-// Run worlds [first, first + count) (or first + list[i] for i < count when list is
-// non-null) of the stream (key, tag, inst).  Returns the number of worlds whose
-// per-warp buffers overflowed (their relative indices are in out.deferred); those
-// worlds contributed nothing.
-void launch_worlds(imin_ctx *ctx, const imin_graph *g, const QueryDev &q, uint32_t flags,
-                   uint64_t first, uint32_t count, const uint32_t *list, const SlotCfg &cfg,
-                   void *slot_base, const WorldOut &out, uint32_t *claim_counter);
+int world_kernel_blocks_per_sm(uint32_t flags, int U);
+
+// One stream of worlds of one query on one graph: worlds [first, first + count)
+// (or first + list[i]) of (key, tag, inst), with its own outputs and stopping rule.
+struct WTask {
+    const int32_t *row_ptr;
+    const uint4 *ce;
+    const int32_t *in_ptr, *in_src, *in_eid;
+    const uint32_t *in_thr;
+    int32_t n;
+    QueryDev q;
+    uint64_t first;
+    uint32_t count;
+    const uint32_t *list;
+    WorldOut out;
+};
+
+WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t count,
+                const uint32_t *list, const WorldOut &out);
+
+// One persistent launch over several tasks (all of the mode given by `flags`).
+// d_tasks holds the descriptors; d_claim / d_done are zeroed per-task counters.
+void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_graph *g0,
+                  uint32_t flags, const SlotCfg &cfg, void *slot_base, uint32_t *d_claim,
+                  uint32_t *d_done);
 
 // ---------------------------------------------------------------------------
 // Utilities (graph.cu)

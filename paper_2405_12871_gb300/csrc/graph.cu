@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 unsigned long long g_kernel_launches = 0;
 
@@ -47,10 +48,10 @@ void DBuf::release()
     bytes = 0;
 }
 
-void DBuf::ensure(imin_ctx *c, size_t need, bool keep)
+void DBuf::ensure(imin_ctx *c, size_t need, bool keep, bool exact)
 {
     if (need <= bytes && p) return;
-    size_t nb = std::max(need, bytes + bytes / 2);
+    size_t nb = exact ? need : std::max(need, bytes + bytes / 2);
     nb = (nb + 255) & ~(size_t)255;
     void *np = dev_alloc(c, nb);
     if (keep && p && bytes) {
@@ -208,6 +209,16 @@ __global__ void make_thr(const float *prob, uint32_t *thr, int64_t m, int64_t m4
     thr[e] = t;
 }
 
+// interleave: group g -> {col[4g..4g+3], thr[4g..4g+3]} (32 bytes)
+__global__ void make_ce(const int32_t *col, const uint32_t *thr, int64_t groups, uint32_t *ce)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // one edge slot
+    if (i >= groups * 4) return;
+    const int64_t g = i >> 2, c = i & 3;
+    ce[8 * g + c] = (uint32_t)col[i];
+    ce[8 * g + 4 + c] = thr[i];
+}
+
 __global__ void pad_col(int32_t *col, int64_t m, int64_t m4)
 {
     const int64_t e = m + threadIdx.x;
@@ -270,6 +281,32 @@ void build_device_graph(imin_graph *g, const float *h_prob)
         IM_CHECK_LAUNCH();
     } else {
         IM_CUDA(cudaMemsetAsync(g->thr.p, 0, 16, st));
+    }
+    // interleaved edge groups for the sampler
+    {
+        const int64_t groups = std::max<int64_t>(m4, 4) / 4;
+        g->ce_bytes = (size_t)groups * 32;
+        g->ce.ensure(ctx, g->ce_bytes);
+        make_ce<<<(unsigned)((groups * 4 + 255) / 256), 256, 0, st>>>(
+            g->col.as<int32_t>(), g->thr.as<uint32_t>(), groups, g->ce.as<uint32_t>());
+        IM_CHECK_LAUNCH();
+    }
+    // L2 persistence (context-wide limit, restored by imin_destroy); only when asked for
+    if (!ctx->persist_set && std::getenv("IMIN_L2_PERSIST")) {
+        int maxp = 0, maxw = 0;
+        if (cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, ctx->device) == cudaSuccess &&
+            cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, ctx->device) == cudaSuccess &&
+            maxp > 0 && maxw > 0) {
+            size_t prev = 0;
+            if (cudaDeviceGetLimit(&prev, cudaLimitPersistingL2CacheSize) == cudaSuccess &&
+                cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, (size_t)maxp) == cudaSuccess) {
+                ctx->prev_persist_limit = prev;
+                ctx->persist_set = true;
+                ctx->l2_persist_bytes = (size_t)maxp;
+                ctx->l2_window_bytes = (size_t)maxw;
+            }
+        }
+        cudaGetLastError();
     }
     // reverse index
     DBuf tmp;

@@ -25,20 +25,16 @@
 // so the result equals Lengauer-Tarjan's.
 #include "common.cuh"
 
+#include <algorithm>
+#include <cstdlib>
+
 namespace {
 
 struct KArgs {
-    const int32_t *row_ptr;
-    const int4 *col4;
-    const uint4 *thr4;
-    const int32_t *in_ptr, *in_src, *in_eid;
-    const uint32_t *in_thr;
-    int32_t n;
-    QueryDev q;
-    uint64_t first;
-    uint32_t count;
-    const uint32_t *list;
-    uint32_t *claim;
+    const WTask *tasks;        // device array of task descriptors
+    int ntasks;
+    uint32_t *task_claim;      // per task: next world to claim
+    uint32_t *task_done;       // per task: 1 once exhausted (or stopped)
     char *slot_base;
     size_t slot_bytes;
     size_t bm_words;
@@ -46,7 +42,6 @@ struct KArgs {
     size_t off_queue, off_loc, off_lvl, off_par, off_idom, off_size, off_pre, off_cur, off_lstart,
         off_pu, off_pv, off_bm2, off_q2;
     uint32_t flags;
-    WorldOut out;
 };
 
 __device__ __forceinline__ int warp_incl_scan(int x, int lane)
@@ -109,8 +104,10 @@ __device__ unsigned long long reserve(unsigned long long *cursor, unsigned long 
     return ~0ull;
 }
 
-template <bool LOWER, bool UPPER, bool STOP>
-__global__ void __launch_bounds__(256) world_kernel(const KArgs a)
+// reach-only and upper-bound worlds run 32 warps per SM (<= 64 registers); the lower bound
+// keeps more state per world and runs fewer, larger warps
+template <int U, bool LOWER, bool UPPER, bool STOP>
+__global__ void __launch_bounds__(256, LOWER ? 1 : 4) world_kernel(const KArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -138,28 +135,60 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
         bm2 = reinterpret_cast<uint32_t *>(slot + a.off_bm2);
         Q2 = reinterpret_cast<int32_t *>(slot + a.off_q2);
     }
-    const int nS = a.q.nS;
     const int qcap = a.qcap;
-    const uint32_t klo = (uint32_t)a.q.key, khi = (uint32_t)(a.q.key >> 32);
-    const uint32_t tag = a.q.tag, inst = a.q.inst;
     const bool store = (a.flags & WF_STORE) != 0;
+    int ti = (int)(wid % (size_t)a.ntasks);
 
     for (;;) {
+        // lane 0 claims the next world of an unfinished task, starting with the task the
+        // warp worked on last; a task is finished when its range is used up or (stopping
+        // rule) its running spread has reached its threshold
+        int got = -1;
         uint32_t rel = 0xffffffffu;
         if (lane == 0) {
-            bool stop = false;
-            if (STOP) stop = *(volatile unsigned long long *)(a.out.acc + 3) >= a.out.stop_T;
-            if (!stop) rel = atomicAdd(a.claim, 1u);
+            for (int scan = 0; scan < a.ntasks; ++scan) {
+                const int t = (ti + scan) % a.ntasks;
+                if (*(volatile uint32_t *)(a.task_done + t)) continue;
+                const WTask *tp = a.tasks + t;
+                if (STOP && *(volatile unsigned long long *)(tp->out.acc + 3) >= tp->out.stop_T) {
+                    a.task_done[t] = 1u;
+                    continue;
+                }
+                const uint32_t r = atomicAdd(a.task_claim + t, 1u);
+                if (r >= tp->count) {
+                    a.task_done[t] = 1u;
+                    continue;
+                }
+                got = t;
+                rel = r;
+                break;
+            }
         }
+        got = __shfl_sync(IMIN_FULL, got, 0);
         rel = __shfl_sync(IMIN_FULL, rel, 0);
-        if (rel >= a.count) break;
+        if (got < 0) break;
+        ti = got;
+        const WTask &T = a.tasks[ti];
+        // the fields the traversal touches, read once per world
+        const int32_t *const row_ptr = T.row_ptr;
+        const uint4 *const ce = T.ce;
+        const uint32_t *const seed_bm = T.q.seed_bm;
+        const uint32_t *const blocked_bm = T.q.blocked_bm;
+        const int nS = T.q.nS;
+        const uint32_t klo = (uint32_t)T.q.key, khi = (uint32_t)(T.q.key >> 32);
+        const uint32_t tag = T.q.tag, inst = T.q.inst;
         // wrel: index of the world relative to `first` (outputs are indexed by it)
-        const uint32_t wrel = a.list ? a.list[rel] : rel;
-        const uint32_t j = (uint32_t)(a.first + (uint64_t)wrel);
+        const uint32_t wrel = T.list ? (T.list[rel] & 0x7fffffffu) : rel;
+        const uint32_t j = (uint32_t)(T.first + (uint64_t)wrel);
 
         // ---- 1. masked reach BFS -------------------------------------------------
+        if (!LOWER && !UPPER)
+            for (int i = lane; i < T.q.nB; i += 32) {
+                const int v = T.q.B[i];
+                atomicOr(&bm[v >> 5], 1u << (v & 31));
+            }
         for (int i = lane; i < nS; i += 32) {
-            const int s = a.q.S[i];
+            const int s = T.q.S[i];
             atomicOr(&bm[s >> 5], 1u << (s & 31));
             Q[i] = s;
             if (LOWER) {
@@ -180,67 +209,98 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
                 int b = 0, e = 0, cnt = 0;
                 if (i < fend) {
                     const int u = Q[i];
-                    b = a.row_ptr[u];
-                    e = a.row_ptr[u + 1];
+                    b = row_ptr[u];
+                    e = row_ptr[u + 1];
                     if (e > b) cnt = ((e + 3) >> 2) - (b >> 2);
                     wedges += (unsigned long long)(e - b);
                 }
                 const int incl = warp_incl_scan(cnt, lane);
                 const int total = __shfl_sync(IMIN_FULL, incl, 31);
-                for (int t0 = 0; t0 < total; t0 += 32) {
-                    const int t = t0 + lane;
-                    const int lo = owner_lane(incl, t);
-                    const int ob = __shfl_sync(IMIN_FULL, b, lo);
-                    const int oe = __shfl_sync(IMIN_FULL, e, lo);
-                    const int ostart = __shfl_sync(IMIN_FULL, incl - cnt, lo);
-                    const int oi = base + lo;
-                    int nv[4] = {-1, -1, -1, -1};
-                    int pvv[4] = {-1, -1, -1, -1};
-                    if (t < total) {
-                        const int g = (ob >> 2) + (t - ostart);
-                        const int4 c4 = __ldg(a.col4 + g);
-                        const uint4 t4 = __ldg(a.thr4 + g);
-                        const uint4 w = philox10(make_uint4((uint32_t)g, j, tag, inst), klo, khi);
-                        const int cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                        const uint32_t tv[4] = {t4.x, t4.y, t4.z, t4.w};
-                        const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+                // U groups per lane per step: every lane issues the loads of all its
+                // groups before any coin or atomic, so U loads are in flight per lane.
+                for (int t0 = 0; t0 < total; t0 += 32 * U) {
+                    int gq[U], obq[U], oeq[U], oiq[U];
+                    bool act[U];
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            const int ec = (g << 2) + c;
-                            if (ec < ob || ec >= oe) continue;
-                            if ((wv[c] >> 8) >= tv[c]) continue;
-                            const int v = cv[c];
-                            if (a.q.blocked_bm && bit_test(a.q.blocked_bm, v)) continue;
-                            if (LOWER && !bit_test(a.q.seed_bm, v)) pvv[c] = v;
-                            const uint32_t bit = 1u << (v & 31);
-                            const uint32_t old = atomicOr(&bm[v >> 5], bit);
-                            if (!(old & bit)) nv[c] = v;
+                    for (int u = 0; u < U; ++u) {
+                        const int t = t0 + u * 32 + lane;
+                        const int lo = owner_lane(incl, t);
+                        obq[u] = __shfl_sync(IMIN_FULL, b, lo);
+                        oeq[u] = __shfl_sync(IMIN_FULL, e, lo);
+                        const int ostart = __shfl_sync(IMIN_FULL, incl - cnt, lo);
+                        oiq[u] = base + lo;
+                        act[u] = t < total;
+                        gq[u] = (obq[u] >> 2) + (t - ostart);
+                    }
+                    int4 c4[U];
+                    uint4 t4[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (act[u]) {
+                            const int4 *p = reinterpret_cast<const int4 *>(ce + 2 * (size_t)gq[u]);
+                            c4[u] = __ldg(p);
+                            t4[u] = __ldg(reinterpret_cast<const uint4 *>(p + 1));
+                        } else {
+                            c4[u] = make_int4(0, 0, 0, 0);
+                            t4[u] = make_uint4(0, 0, 0, 0);
                         }
                     }
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const uint32_t bal = __ballot_sync(IMIN_FULL, nv[c] >= 0);
-                        if (bal) {
-                            const int pos = tail + __popc(bal & lt_mask);
-                            if (nv[c] >= 0 && pos < qcap) {
-                                Q[pos] = nv[c];
-                                if (LOWER) {
-                                    loc[nv[c]] = pos;
-                                    lvl[pos] = L + 1;
-                                    par[pos] = oi;
-                                }
+                    for (int u = 0; u < U; ++u) {
+                        int nv[4] = {-1, -1, -1, -1};
+                        int pvv[4] = {-1, -1, -1, -1};
+                        if (act[u]) {
+                            const int g = gq[u];
+                            const uint4 w = philox10(make_uint4((uint32_t)g, j, tag, inst), klo, khi);
+                            const int cv[4] = {c4[u].x, c4[u].y, c4[u].z, c4[u].w};
+                            const uint32_t tv[4] = {t4[u].x, t4[u].y, t4[u].z, t4[u].w};
+                            const uint32_t wv[4] = {w.x, w.y, w.z, w.w};
+                            bool ok[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c) {
+                                const int ec = (g << 2) + c;
+                                ok[c] = ec >= obq[u] && ec < oeq[u] && (wv[c] >> 8) < tv[c];
+                                // reach-only worlds pre-mark blocked nodes as visited
+                                if ((LOWER || UPPER) && ok[c] && blocked_bm)
+                                    ok[c] = !bit_test(blocked_bm, cv[c]);
+                                if (LOWER && ok[c] && !bit_test(seed_bm, cv[c])) pvv[c] = cv[c];
                             }
-                            tail += __popc(bal);
+                            // the (rare) claims are independent: issue them back to back
+                            uint32_t old[4];
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                old[c] = ok[c] ? atomicOr(&bm[cv[c] >> 5], 1u << (cv[c] & 31))
+                                               : 0xffffffffu;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if (!((old[c] >> (cv[c] & 31)) & 1u)) nv[c] = cv[c];
                         }
-                        if (LOWER) {
-                            const uint32_t pb = __ballot_sync(IMIN_FULL, pvv[c] >= 0);
-                            if (pb) {
-                                const int pp = npairs + __popc(pb & lt_mask);
-                                if (pvv[c] >= 0 && pp < a.ecap) {
-                                    pu[pp] = oi;
-                                    pv[pp] = pvv[c];
+                        const int oi = oiq[u];
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            const uint32_t bal = __ballot_sync(IMIN_FULL, nv[c] >= 0);
+                            if (bal) {
+                                const int pos = tail + __popc(bal & lt_mask);
+                                if (nv[c] >= 0 && pos < qcap) {
+                                    Q[pos] = nv[c];
+                                    if (LOWER) {
+                                        loc[nv[c]] = pos;
+                                        lvl[pos] = L + 1;
+                                        par[pos] = oi;
+                                    }
                                 }
-                                npairs += __popc(pb);
+                                tail += __popc(bal);
+                            }
+                            if (LOWER) {
+                                const uint32_t pb = __ballot_sync(IMIN_FULL, pvv[c] >= 0);
+                                if (pb) {
+                                    const int pp = npairs + __popc(pb & lt_mask);
+                                    if (pvv[c] >= 0 && pp < a.ecap) {
+                                        pu[pp] = oi;
+                                        pv[pp] = pvv[c];
+                                    }
+                                    npairs += __popc(pb);
+                                }
                             }
                         }
                     }
@@ -287,7 +347,7 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
                 __syncwarp();
                 if (!__any_sync(IMIN_FULL, changed)) break;
                 if (pass > (1 << 20)) {
-                    if (lane == 0) atomicOr(a.out.err, DERR_TIMEOUT);
+                    if (lane == 0) atomicOr(T.out.err, DERR_TIMEOUT);
                     break;
                 }
             }
@@ -304,13 +364,13 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
 
         // ---- 3. Global Sampling target and LRR set --------------------------------
         int tail2 = 0;
-        if (UPPER && !ovf && a.q.nVs > 0) {
+        if (UPPER && !ovf && T.q.nVs > 0) {
             int tnode = -1;
             if (lane == 0) {
                 const uint4 w = philox10(make_uint4(0xFFFFFFFFu, j, tag, inst), klo, khi);
                 const unsigned long long r64 = ((unsigned long long)w.y << 32) | w.x;
-                const unsigned long long idx = __umul64hi(r64, (unsigned long long)a.q.nVs);
-                const int t = a.q.Vs[idx];
+                const unsigned long long idx = __umul64hi(r64, (unsigned long long)T.q.nVs);
+                const int t = T.q.Vs[idx];
                 if (bit_test_cg(bm, t)) tnode = t;
             }
             tnode = __shfl_sync(IMIN_FULL, tnode, 0);
@@ -329,8 +389,8 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
                         int b = 0, cnt = 0;
                         if (i < fend) {
                             const int v = Q2[i];
-                            b = a.in_ptr[v];
-                            cnt = a.in_ptr[v + 1] - b;
+                            b = T.in_ptr[v];
+                            cnt = T.in_ptr[v + 1] - b;
                         }
                         const int incl = warp_incl_scan(cnt, lane);
                         const int total = __shfl_sync(IMIN_FULL, incl, 31);
@@ -342,10 +402,10 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
                             int nu = -1;
                             if (t < total) {
                                 const int idx = ob + (t - ostart);
-                                const int u = __ldg(a.in_src + idx);
-                                if (bit_test_cg(bm, u) && !bit_test(a.q.seed_bm, u)) {
-                                    const int eid = __ldg(a.in_eid + idx);
-                                    const uint32_t th = __ldg(a.in_thr + idx);
+                                const int u = __ldg(T.in_src + idx);
+                                if (bit_test_cg(bm, u) && !bit_test(seed_bm, u)) {
+                                    const int eid = __ldg(T.in_eid + idx);
+                                    const uint32_t th = __ldg(T.in_thr + idx);
                                     const uint4 w = philox10(
                                         make_uint4((uint32_t)eid >> 2, j, tag, inst), klo, khi);
                                     if ((pick_word(w, eid & 3) >> 8) < th) {
@@ -374,14 +434,15 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
         }
 
         // ---- 4. reserve store space -----------------------------------------------
+        const bool slot_ovf = ovf;
         unsigned long long sbase = 0;
         if (!ovf && store && (LOWER || UPPER)) {
             if (lane == 0) {
                 if (LOWER)
-                    sbase = reserve(a.out.rec_cursor, (unsigned long long)(tail - nS), a.out.rec_cap);
+                    sbase = reserve(T.out.rec_cursor, (unsigned long long)(tail - nS), T.out.rec_cap);
                 else
-                    sbase = tail2 > 0 ? reserve(a.out.set_cursor, (unsigned long long)tail2,
-                                                a.out.set_cap)
+                    sbase = tail2 > 0 ? reserve(T.out.set_cursor, (unsigned long long)tail2,
+                                                T.out.set_cap)
                                       : 0ull;
             }
             sbase = __shfl_sync(IMIN_FULL, sbase, 0);
@@ -395,11 +456,12 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
             if (UPPER)
                 for (size_t w = lane; w < a.bm_words; w += 32) bm2[w] = 0;
             if (lane == 0) {
-                const uint32_t d = atomicAdd(a.out.n_deferred, 1u);
-                if (d < a.out.deferred_cap)
-                    a.out.deferred[d] = wrel;
+                const uint32_t d = atomicAdd(T.out.n_deferred, 1u);
+                // the top bit marks worlds that need a large slot (not just store room)
+                if (d < T.out.deferred_cap)
+                    T.out.deferred[d] = wrel | (slot_ovf ? 0x80000000u : 0u);
                 else
-                    atomicOr(a.out.err, DERR_INTERNAL);
+                    atomicOr(T.out.err, DERR_INTERNAL);
             }
             __syncwarp();
             continue;
@@ -407,9 +469,9 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
 
         // ---- 5. outputs ---------------------------------------------------------------
         if (LOWER) {
-            if (a.out.credit_L)
+            if (T.out.credit_L)
                 for (int i = nS + lane; i < tail; i += 32)
-                    atomicAdd(a.out.credit_L + Q[i], (unsigned long long)__ldcg(sz + i));
+                    atomicAdd(T.out.credit_L + Q[i], (unsigned long long)__ldcg(sz + i));
             if (store) {
                 // DT preorder, level by level: roots (idom = s or a seed) get consecutive
                 // ranges; a child starts after its parent and the earlier siblings' subtrees.
@@ -437,9 +499,9 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
                             }
                             pre[i] = pr;
                             const unsigned long long r = sbase + (unsigned long long)pr;
-                            a.out.rec_node[r] = Q[i];
-                            a.out.rec_par[r] = poff;
-                            a.out.rec_size[r] = size_i;
+                            T.out.rec_node[r] = Q[i];
+                            T.out.rec_par[r] = poff;
+                            T.out.rec_size[r] = size_i;
                         }
                         rootbase += rtot;
                     }
@@ -448,31 +510,33 @@ __global__ void __launch_bounds__(256) world_kernel(const KArgs a)
             }
         }
         if (UPPER) {
-            if (a.out.credit_U)
-                for (int i = lane; i < tail2; i += 32) atomicAdd(a.out.credit_U + Q2[i], 1ull);
+            if (T.out.credit_U)
+                for (int i = lane; i < tail2; i += 32) atomicAdd(T.out.credit_U + Q2[i], 1ull);
             if (store) {
-                for (int i = lane; i < tail2; i += 32) a.out.set_elem[sbase + i] = Q2[i];
+                for (int i = lane; i < tail2; i += 32) T.out.set_elem[sbase + i] = Q2[i];
                 if (lane == 0) {
-                    a.out.set_off[wrel] = sbase;
-                    a.out.set_len[wrel] = (uint32_t)tail2;
+                    T.out.set_off[wrel] = sbase;
+                    T.out.set_len[wrel] = (uint32_t)tail2;
                 }
             }
             for (int i = lane; i < tail2; i += 32) bm2[Q2[i] >> 5] = 0;
         }
         if (a.flags & WF_REACH)
-            for (int i = lane; i < tail; i += 32) atomicAdd(a.out.reach + Q[i], 1ull);
+            for (int i = lane; i < tail; i += 32) atomicAdd(T.out.reach + Q[i], 1ull);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wedges += __shfl_xor_sync(IMIN_FULL, wedges, o);
         if (lane == 0) {
-            atomicAdd(a.out.acc + 0, (unsigned long long)tail);
-            atomicAdd(a.out.acc + 1, wedges);
-            if (UPPER && tail2 > 0) atomicAdd(a.out.acc + 2, 1ull);
-            if (STOP) atomicAdd(a.out.acc + 3, (unsigned long long)tail);
-            atomicAdd(a.out.acc + 4, 1ull);
-            if (a.out.world_spread) a.out.world_spread[wrel] = (uint32_t)tail;
+            atomicAdd(T.out.acc + 0, (unsigned long long)tail);
+            atomicAdd(T.out.acc + 1, wedges);
+            if (UPPER && tail2 > 0) atomicAdd(T.out.acc + 2, 1ull);
+            if (STOP) atomicAdd(T.out.acc + 3, (unsigned long long)tail);
+            atomicAdd(T.out.acc + 4, 1ull);
+            if (T.out.world_spread) T.out.world_spread[wrel] = (uint32_t)tail;
         }
         __syncwarp();
         for (int i = lane; i < tail; i += 32) bm[Q[i] >> 5] = 0;
+        if (!LOWER && !UPPER)
+            for (int i = lane; i < T.q.nB; i += 32) bm[T.q.B[i] >> 5] = 0;
         __syncwarp();
     }
 }
@@ -493,25 +557,69 @@ size_t SlotCfg::bytes_per_slot() const
     return b;
 }
 
-void launch_worlds(imin_ctx *ctx, const imin_graph *g, const QueryDev &q, uint32_t flags,
-                   uint64_t first, uint32_t count, const uint32_t *list, const SlotCfg &cfg,
-                   void *slot_base, const WorldOut &out, uint32_t *claim_counter)
+// resident 256-thread blocks per SM of the instantiation a launch would use
+int world_kernel_blocks_per_sm(uint32_t flags, int U)
 {
-    if (count == 0) return;
+    const bool lower = (flags & WF_LOWER) != 0, upper = (flags & WF_UPPER) != 0,
+               stop = (flags & WF_STOP) != 0;
+    int nb = 0;
+    cudaError_t e = cudaSuccess;
+#define IM_OCC(UU)                                                                               \
+    do {                                                                                         \
+        if (lower && upper)                                                                      \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, world_kernel<UU, true, true, false>, 256, 0);   \
+        else if (lower)                                                                          \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, world_kernel<UU, true, false, false>, 256, 0);  \
+        else if (upper)                                                                          \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, world_kernel<UU, false, true, false>, 256, 0);  \
+        else if (stop)                                                                           \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, world_kernel<UU, false, false, true>, 256, 0);  \
+        else                                                                                     \
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, world_kernel<UU, false, false, false>, 256, 0); \
+    } while (0)
+    if (U >= 4)
+        IM_OCC(4);
+    else if (U == 2)
+        IM_OCC(2);
+    else
+        IM_OCC(1);
+#undef IM_OCC
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return nb < 1 ? 1 : nb;
+}
+
+WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t count,
+                const uint32_t *list, const WorldOut &out)
+{
+    WTask t;
+    t.row_ptr = g->row_ptr.as<int32_t>();
+    t.ce = g->ce.as<uint4>();
+    t.in_ptr = g->in_ptr.as<int32_t>();
+    t.in_src = g->in_src.as<int32_t>();
+    t.in_eid = g->in_eid.as<int32_t>();
+    t.in_thr = g->in_thr.as<uint32_t>();
+    t.n = g->n;
+    t.q = q;
+    t.first = first;
+    t.count = count;
+    t.list = list;
+    t.out = out;
+    return t;
+}
+
+void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_graph *g,
+                  uint32_t flags, const SlotCfg &cfg, void *slot_base, uint32_t *d_claim,
+                  uint32_t *d_done)
+{
+    if (ntasks <= 0) return;
     KArgs a;
-    a.row_ptr = g->row_ptr.as<int32_t>();
-    a.col4 = g->col.as<int4>();
-    a.thr4 = g->thr.as<uint4>();
-    a.in_ptr = g->in_ptr.as<int32_t>();
-    a.in_src = g->in_src.as<int32_t>();
-    a.in_eid = g->in_eid.as<int32_t>();
-    a.in_thr = g->in_thr.as<uint32_t>();
-    a.n = g->n;
-    a.q = q;
-    a.first = first;
-    a.count = count;
-    a.list = list;
-    a.claim = claim_counter;
+    a.tasks = d_tasks;
+    a.ntasks = ntasks;
+    a.task_claim = d_claim;
+    a.task_done = d_done;
     a.slot_base = reinterpret_cast<char *>(slot_base);
     a.slot_bytes = cfg.bytes_per_slot();
     a.bm_words = cfg.bm_words;
@@ -539,23 +647,59 @@ void launch_worlds(imin_ctx *ctx, const imin_graph *g, const QueryDev &q, uint32
         a.off_q2 = off;     off += al16((size_t)cfg.qcap * 4);
     }
     a.flags = flags;
-    a.out = out;
 
     const int threads = 256;
     const int blocks = cfg.warps / (threads / 32);
-    IM_CUDA(cudaMemsetAsync(claim_counter, 0, sizeof(uint32_t), ctx->stream));
     const bool lower = (flags & WF_LOWER) != 0, upper = (flags & WF_UPPER) != 0,
                stop = (flags & WF_STOP) != 0;
-    if (lower && upper) {
-        world_kernel<true, true, false><<<blocks, threads, 0, ctx->stream>>>(a);
-    } else if (lower) {
-        world_kernel<true, false, false><<<blocks, threads, 0, ctx->stream>>>(a);
-    } else if (upper) {
-        world_kernel<false, true, false><<<blocks, threads, 0, ctx->stream>>>(a);
-    } else if (stop) {
-        world_kernel<false, false, true><<<blocks, threads, 0, ctx->stream>>>(a);
-    } else {
-        world_kernel<false, false, false><<<blocks, threads, 0, ctx->stream>>>(a);
+    const int U = cfg.groups_per_lane;
+    // keep the interleaved edge array resident in L2 while worlds are traversed
+    cudaLaunchAttribute attr[1];
+    int nattr = 0;
+    // tuning hook: IMIN_L2_PERSIST=<hit ratio in percent> enables the window (off by default:
+    // on the 1M-node Chung-Lu workload the carve-out left too little L2 for the bitmaps)
+    double hit_pct = 0.0;
+    if (const char *env = std::getenv("IMIN_L2_PERSIST")) hit_pct = std::strtod(env, nullptr);
+    if (hit_pct > 0.0 && ctx->l2_window_bytes > 0 && g && g->ce.p) {
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = g->ce.p;
+        attr[0].val.accessPolicyWindow.num_bytes = std::min(ctx->l2_window_bytes, g->ce_bytes);
+        attr[0].val.accessPolicyWindow.hitRatio =
+            (float)std::min(hit_pct / 100.0, (double)ctx->l2_persist_bytes /
+                                                 (double)attr[0].val.accessPolicyWindow.num_bytes);
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        nattr = 1;
     }
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(blocks);
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = ctx->stream;
+    lc.attrs = nattr ? attr : nullptr;
+    lc.numAttrs = nattr;
+#define IM_WKX(UU, L_, U_, S_) IM_CUDA(cudaLaunchKernelEx(&lc, world_kernel<UU, L_, U_, S_>, a))
+#undef IM_WK
+#define IM_WK(UU)                                        \
+    do {                                                 \
+        if (lower && upper)                              \
+            IM_WKX(UU, true, true, false);               \
+        else if (lower)                                  \
+            IM_WKX(UU, true, false, false);              \
+        else if (upper)                                  \
+            IM_WKX(UU, false, true, false);              \
+        else if (stop)                                   \
+            IM_WKX(UU, false, false, true);              \
+        else                                             \
+            IM_WKX(UU, false, false, false);             \
+    } while (0)
+    if (U >= 4)
+        IM_WK(4);
+    else if (U == 2)
+        IM_WK(2);
+    else
+        IM_WK(1);
+#undef IM_WKX
+#undef IM_WK
     IM_CHECK_LAUNCH();
 }
