@@ -200,6 +200,28 @@ typedef struct imin_result {
 int imin_solve(imin_graph *g, const int32_t *S, int32_t nS, int32_t k, double eps, double delta,
                const imin_solve_opts *opts, imin_result *res);
 
+/* One query of a batch: the arguments of imin_solve.  The blocker arrays of the
+ * matching imin_result are caller-allocated as for imin_solve. */
+typedef struct imin_query {
+    imin_graph *g;          /* a graph loaded through the same context */
+    const int32_t *S;       /* host int32[nS] */
+    int32_t nS;
+    int32_t k;
+    double eps, delta;
+    imin_solve_opts opts;
+} imin_query;
+
+/* Batch engine: solve n_inst independent queries (possibly on different graphs of
+ * the same context) together.  Each stage of Algorithm 1 -- the spread estimates,
+ * every doubling round of LSBM and GSBM, the final estimates -- runs as one
+ * persistent launch over all instances still in that stage, and every Max-Coverage
+ * round step is one launch for all instances.  results[i] is exactly what
+ * imin_solve returns for queries[i] alone (worlds are addressed by index; the
+ * batch only changes how they are scheduled); ms_stage and kernel_ms report the
+ * whole batch.  Errors: as imin_solve; on error no result is complete. */
+int imin_solve_batch(imin_ctx *ctx, int32_t n_inst, const imin_query *queries,
+                     imin_result *results);
+
 /* Static description of a status code. */
 const char *imin_strerror(int status);
 

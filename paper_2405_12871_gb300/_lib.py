@@ -19,7 +19,8 @@ VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 
 # names the library must export (checked by the CPU tests against include/imin.h)
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
-           "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc"]
+           "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc",
+           "imin_solve_batch"]
 NOALLOC_MAX_NODES = 2_000_000
 
 
@@ -58,6 +59,12 @@ class Result(C.Structure):
         ("kernel_ms", C.c_double * 4), ("reach_nodes", C.c_uint64), ("reach_edges", C.c_uint64),
         ("reach_launches", C.c_uint64), ("kernel_launches", C.c_uint64),
     ]
+
+
+class Query(C.Structure):
+    _fields_ = [("g", C.c_void_p), ("S", C.POINTER(C.c_int32)), ("nS", C.c_int32),
+                ("k", C.c_int32), ("eps", C.c_double), ("delta", C.c_double),
+                ("opts", SolveOpts)]
 
 
 _lib = None
@@ -103,6 +110,8 @@ def load(build_if_missing: bool = True):
                                             C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                             C.c_void_p, C.c_void_p, P(C.c_uint64), C.c_void_p]
     L.imin_sample_reach_noalloc.restype = C.c_int
+    L.imin_solve_batch.argtypes = [C.c_void_p, C.c_int32, P(Query), P(Result)]
+    L.imin_solve_batch.restype = C.c_int
     _lib = L
     return L
 
@@ -222,6 +231,48 @@ def imin_solve(ctx, g, S, k, eps, delta, beta=0.1, gamma=0.1, key=0, inst=0,
     return d
 
 
+def _result_dict(r, arrs):
+    d = {}
+    for name, _ in Result._fields_:
+        if name in ("blockers", "B_L", "B_U", "B_R"):
+            continue
+        v = getattr(r, name)
+        d[name] = list(v) if hasattr(v, "__len__") else v
+    d["blockers"] = arrs[0][: r.n_blockers].copy()
+    d["B_L"] = arrs[1][: r.nBL].copy()
+    d["B_U"] = arrs[2][: r.nBU].copy()
+    d["B_R"] = arrs[3][: r.nBR].copy()
+    return d
+
+
+def imin_solve_batch(ctx, queries):
+    """queries: list of dicts with keys g (graph handle), S, k, eps, delta and optional
+    beta, gamma, key, inst, variant, fixed_theta.  Returns one result dict per query."""
+    L = load()
+    n = len(queries)
+    qs = (Query * max(n, 1))()
+    rs = (Result * max(n, 1))()
+    keep = []
+    for i, q in enumerate(queries):
+        S = _as_i32(q["S"])
+        arrs = [np.zeros(max(int(q["k"]), 1), np.int32) for _ in range(4)]
+        keep.append((S, arrs))
+        qs[i].g = q["g"].value if isinstance(q["g"], C.c_void_p) else q["g"]
+        qs[i].S = _i32p(S)
+        qs[i].nS = len(S)
+        qs[i].k = int(q["k"])
+        qs[i].eps = float(q["eps"])
+        qs[i].delta = float(q["delta"])
+        qs[i].opts = SolveOpts(float(q.get("beta", 0.1)), float(q.get("gamma", 0.1)),
+                               int(q.get("key", 0)), int(q.get("inst", 0)),
+                               VARIANTS[q.get("variant", "sandimin")], int(q.get("fixed_theta", 0)))
+        rs[i].blockers, rs[i].B_L, rs[i].B_U, rs[i].B_R = [
+            a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
+    rc = L.imin_solve_batch(ctx, n, qs, rs)
+    _check(ctx, rc, "imin_solve_batch")
+    return [_result_dict(rs[i], keep[i][1]) for i in range(n)]
+
+
 class Context:
     """Convenience owner of an imin_ctx (and the graphs loaded through it)."""
 
@@ -230,6 +281,15 @@ class Context:
 
     def load_graph(self, g):
         return Graph(self, g)
+
+    def solve_batch(self, queries):
+        """queries: list of (Graph, S, k, eps, delta, kwargs)."""
+        qs = []
+        for G, S, k, eps, delta, kw in queries:
+            d = dict(g=G.h, S=S, k=k, eps=eps, delta=delta)
+            d.update(kw)
+            qs.append(d)
+        return imin_solve_batch(self.h, qs)
 
     def close(self):
         if self.h:

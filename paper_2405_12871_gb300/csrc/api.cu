@@ -27,6 +27,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <memory>
 #include <numeric>
 
 void build_device_graph(imin_graph *g, const float *h_prob);
@@ -501,39 +502,43 @@ void cp_reserve(imin_ctx *ctx, CpStore &c, unsigned long long need)
 }
 
 struct CpJob {
+    const imin_graph *g;
+    const Query *q;
     CpStore *c;
     uint32_t tag;
     unsigned long long *credit;   // may be null
+    uint64_t from, to;
+    uint64_t key;
+    uint32_t inst;
+    double per_world;             // expected records per world (sizes the store)
+    SpreadEst *stats;             // may be null
 };
 
 // append worlds [from, to) of each job's tag to its CP collection, one launch for all jobs
-void sample_cp(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<CpJob> &jobs,
-               uint64_t from, uint64_t to, uint64_t key, uint32_t inst, double est_per_world,
-               SpreadEst *stats)
+void sample_cp(imin_ctx *ctx, std::vector<CpJob> &jobs)
 {
-    if (to <= from) return;
-    if (to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
     const size_t nj = jobs.size();
     std::vector<TaskRun> tr(nj);
     std::vector<TaskRun *> tp;
-    std::vector<unsigned long long> before(nj);
     for (size_t i = 0; i < nj; ++i) {
-        CpStore &c = *jobs[i].c;
+        CpJob &J = jobs[i];
+        if (J.to <= J.from) continue;
+        if (J.to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
+        CpStore &c = *J.c;
         c.cursor.ensure(ctx, 16);
         if (c.worlds == 0) {
             IM_CUDA(cudaMemsetAsync(c.cursor.p, 0, 8, ctx->stream));
             c.count = 0;
         }
         const unsigned long long est =
-            (unsigned long long)((double)(to - from) * std::max(est_per_world, 1.0) * 1.25) + 4096;
+            (unsigned long long)((double)(J.to - J.from) * std::max(J.per_world, 1.0) * 1.25) + 4096;
         cp_reserve(ctx, c, (unsigned long long)c.count + est);
-        before[i] = (unsigned long long)c.count;
         TaskRun &t = tr[i];
-        t.g = g;
-        t.q = qdev(q, key, jobs[i].tag, inst);
-        t.first = from;
-        t.count = (uint32_t)(to - from);
-        t.out.credit_L = jobs[i].credit;
+        t.g = J.g;
+        t.q = qdev(*J.q, J.key, J.tag, J.inst);
+        t.first = J.from;
+        t.count = (uint32_t)(J.to - J.from);
+        t.out.credit_L = J.credit;
         t.out.rec_node = c.node.as<int32_t>();
         t.out.rec_par = c.par.as<int32_t>();
         t.out.rec_size = c.size.as<int32_t>();
@@ -541,14 +546,16 @@ void sample_cp(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<C
         t.out.rec_cap = c.cap;
         CpStore *cp = &c;
         TaskRun *self = &t;
-        const unsigned long long b0 = before[i];
-        t.grow = [ctx, cp, self, b0, from, to, g](uint32_t nd) {
+        const unsigned long long b0 = (unsigned long long)c.count;
+        const uint64_t span = J.to - J.from;
+        const int32_t n = J.g->n;
+        t.grow = [ctx, cp, self, b0, span, n](uint32_t nd) {
             unsigned long long used = 0;
             IM_CUDA(cudaMemcpy(&used, cp->cursor.p, 8, cudaMemcpyDeviceToHost));
-            const uint64_t worlds = (to - from) > nd ? (to - from) - nd : 1;
+            const uint64_t worlds = span > nd ? span - nd : 1;
             const unsigned long long avg = (used - b0) / worlds + 1;
             cp_reserve(ctx, *cp, std::max<unsigned long long>(
-                                     2 * cp->cap, used + (unsigned long long)nd * 2 * avg + (unsigned long long)g->n));
+                                     2 * cp->cap, used + (unsigned long long)nd * 2 * avg + (unsigned long long)n));
             self->out.rec_node = cp->node.as<int32_t>();
             self->out.rec_par = cp->par.as<int32_t>();
             self->out.rec_size = cp->size.as<int32_t>();
@@ -556,23 +563,24 @@ void sample_cp(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<C
         };
         tp.push_back(&t);
     }
+    if (tp.empty()) return;
     Runner run(ctx);
     run.run(tp, WF_LOWER | WF_STORE);
     for (size_t i = 0; i < nj; ++i) {
-        CpStore &c = *jobs[i].c;
+        CpJob &J = jobs[i];
+        if (J.to <= J.from) continue;
+        CpStore &c = *J.c;
         unsigned long long used = 0;
         IM_CUDA(cudaMemcpy(&used, c.cursor.p, 8, cudaMemcpyDeviceToHost));
         c.count = (long long)used;
-        c.worlds += to - from;
-        if (stats) {
-            stats->worlds += tr[i].acc[4];
-            stats->edges += tr[i].acc[1];
-            stats->nodes += tr[i].acc[0];
+        c.worlds += J.to - J.from;
+        if (J.stats) {
+            J.stats->worlds += tr[i].acc[4];
+            J.stats->edges += tr[i].acc[1];
+            J.stats->nodes += tr[i].acc[0];
+            J.stats->kernel_ms += run.kernel_ms / (double)tp.size();
+            J.stats->launches += (uint64_t)run.launches;
         }
-    }
-    if (stats) {
-        stats->kernel_ms += run.kernel_ms;
-        stats->launches += (uint64_t)run.launches;
     }
 }
 
@@ -594,21 +602,27 @@ void lrr_reserve(imin_ctx *ctx, LrrStore &L, unsigned long long need_elems, uint
 }
 
 struct LrrJob {
+    const imin_graph *g;
+    const Query *q;
     LrrStore *L;
     uint32_t tag;
     unsigned long long *credit;   // may be null
+    uint64_t from, to;
+    uint64_t key;
+    uint32_t inst;
+    SpreadEst *stats;             // may be null
 };
 
-void sample_lrr(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<LrrJob> &jobs,
-                uint64_t from, uint64_t to, uint64_t key, uint32_t inst, SpreadEst *stats)
+void sample_lrr(imin_ctx *ctx, std::vector<LrrJob> &jobs)
 {
-    if (to <= from) return;
-    if (to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
     const size_t nj = jobs.size();
     std::vector<TaskRun> tr(nj);
     std::vector<TaskRun *> tp;
     for (size_t i = 0; i < nj; ++i) {
-        LrrStore &L = *jobs[i].L;
+        LrrJob &J = jobs[i];
+        if (J.to <= J.from) continue;
+        if (J.to > ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "world index >= 2^31");
+        LrrStore &L = *J.L;
         L.cursor.ensure(ctx, 16);
         if (L.nsets == 0) {
             IM_CUDA(cudaMemsetAsync(L.cursor.p, 0, 8, ctx->stream));
@@ -616,25 +630,27 @@ void sample_lrr(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<
         }
         // start from the average set size seen so far (64 per world before any is known)
         const unsigned long long per = L.nsets ? L.elems / L.nsets + 1 : 64;
-        lrr_reserve(ctx, L, L.elems + (to - from) * per * 2 + 65536, to);
+        lrr_reserve(ctx, L, L.elems + (J.to - J.from) * per * 2 + 65536, J.to);
         TaskRun &t = tr[i];
-        t.g = g;
-        t.q = qdev(q, key, jobs[i].tag, inst);
-        t.first = from;
-        t.count = (uint32_t)(to - from);
-        t.out.credit_U = jobs[i].credit;
+        t.g = J.g;
+        t.q = qdev(*J.q, J.key, J.tag, J.inst);
+        t.first = J.from;
+        t.count = (uint32_t)(J.to - J.from);
+        t.out.credit_U = J.credit;
         t.out.set_elem = L.elem.as<int32_t>();
-        t.out.set_off = L.off.as<unsigned long long>() + from;
-        t.out.set_len = L.len.as<uint32_t>() + from;
+        t.out.set_off = L.off.as<unsigned long long>() + J.from;
+        t.out.set_len = L.len.as<uint32_t>() + J.from;
         t.out.set_cursor = L.cursor.as<unsigned long long>();
         t.out.set_cap = L.cap;
         LrrStore *lp = &L;
         TaskRun *self = &t;
-        t.grow = [ctx, lp, self, from, to, g](uint32_t nd) {
+        const uint64_t from = J.from, to = J.to;
+        const int32_t n = J.g->n;
+        t.grow = [ctx, lp, self, from, to, n](uint32_t nd) {
             unsigned long long used = 0;
             IM_CUDA(cudaMemcpy(&used, lp->cursor.p, 8, cudaMemcpyDeviceToHost));
             lrr_reserve(ctx, *lp, std::max<unsigned long long>(
-                                      2 * lp->cap, used + (unsigned long long)nd * (unsigned long long)g->n), to);
+                                      2 * lp->cap, used + (unsigned long long)nd * (unsigned long long)n), to);
             self->out.set_elem = lp->elem.as<int32_t>();
             self->out.set_off = lp->off.as<unsigned long long>() + from;
             self->out.set_len = lp->len.as<uint32_t>() + from;
@@ -642,23 +658,24 @@ void sample_lrr(imin_ctx *ctx, const imin_graph *g, const Query &q, std::vector<
         };
         tp.push_back(&t);
     }
+    if (tp.empty()) return;
     Runner run(ctx);
     run.run(tp, WF_UPPER | WF_STORE);
     for (size_t i = 0; i < nj; ++i) {
-        LrrStore &L = *jobs[i].L;
+        LrrJob &J = jobs[i];
+        if (J.to <= J.from) continue;
+        LrrStore &L = *J.L;
         unsigned long long used = 0;
         IM_CUDA(cudaMemcpy(&used, L.cursor.p, 8, cudaMemcpyDeviceToHost));
         L.elems = used;
-        L.nsets = (uint32_t)to;
-        if (stats) {
-            stats->worlds += tr[i].acc[4];
-            stats->edges += tr[i].acc[1];
-            stats->nodes += tr[i].acc[0];
+        L.nsets = (uint32_t)J.to;
+        if (J.stats) {
+            J.stats->worlds += tr[i].acc[4];
+            J.stats->edges += tr[i].acc[1];
+            J.stats->nodes += tr[i].acc[0];
+            J.stats->kernel_ms += run.kernel_ms / (double)tp.size();
+            J.stats->launches += (uint64_t)run.launches;
         }
-    }
-    if (stats) {
-        stats->kernel_ms += run.kernel_ms;
-        stats->launches += (uint64_t)run.launches;
     }
 }
 
@@ -695,29 +712,405 @@ void set_bitmap_host(imin_ctx *ctx, DBuf &bm, size_t words, const std::vector<in
     IM_CUDA(cudaMemcpy(bm.p, h.data(), words * 4, cudaMemcpyHostToDevice));
 }
 
-struct GreedyOut {
-    std::vector<int32_t> B;
-    std::vector<unsigned long long> cov, topk;
-    unsigned long long covu = 0;
+// ---------------------------------------------------------------------------
+// Solve (Algorithm 1) as a state machine per instance.  solve_all() advances every
+// instance of a batch stage by stage, so each sampling stage is one launch for all
+// instances and each Max-Coverage round is one launch per round step; imin_solve is
+// a batch of one.  Every instance's result depends on its own query only (worlds are
+// addressed by index), so a query gives the same answer alone and in any batch.
+// ---------------------------------------------------------------------------
+struct Bound {
+    bool active = false;
+    uint64_t th = 0, from = 0, to = 0;
+    int32_t imax = 0, it = 0;
+    double a1 = 0.0, a2 = 0.0, th_max = 0.0;
+    double sL = 0.0, sU = 0.0;
+    unsigned long long cov2 = 0;
+    GreedyOut go;
+    SpreadEst st;
 };
 
-GreedyOut read_greedy(imin_ctx *ctx, GreedyBufs &gb, int32_t k)
+struct Inst {
+    imin_graph *g = nullptr;
+    int32_t k = 0;
+    double eps = 0.0, delta = 0.0, beta = 0.0, gamma = 0.0;
+    uint64_t key = 0, fixed_theta = 0;
+    uint32_t inst = 0;
+    int variant = 0;
+    imin_result *res = nullptr;
+    int32_t *B_L = nullptr, *B_U = nullptr, *B_R = nullptr, *blockers = nullptr;
+    Query q;
+    std::vector<int32_t> ON, BLv, BUv, BRv;
+    double OPT = 0.0, I_hat = 0.0;
+    int32_t nVs = 0;
+    bool done = false, do_L = false, do_U = false, do_R = false;
+    Bound L, U;
+    CpStore C1, C2;
+    LrrStore L1, L2;
+    DBuf credC1, credL1, inB;
+};
+
+void put(int32_t *dst, const std::vector<int32_t> &src)
 {
-    GState st;
-    IM_CUDA(cudaMemcpyAsync(&st, gb.state.p, sizeof(GState), cudaMemcpyDeviceToHost, ctx->stream));
-    IM_CUDA(cudaStreamSynchronize(ctx->stream));
-    GreedyOut o;
-    const int nb = st.nb;
-    o.B.resize(nb);
-    o.cov.resize(nb + 1);
-    o.topk.resize(nb + 1);
-    if (nb > 0) IM_CUDA(cudaMemcpy(o.B.data(), gb.B.p, (size_t)nb * 4, cudaMemcpyDeviceToHost));
-    IM_CUDA(cudaMemcpy(o.cov.data(), gb.cov.p, (size_t)(nb + 1) * 8, cudaMemcpyDeviceToHost));
-    IM_CUDA(cudaMemcpy(o.topk.data(), gb.topk.p, (size_t)(nb + 1) * 8, cudaMemcpyDeviceToHost));
-    o.covu = o.cov[0] + o.topk[0];
-    for (int t = 1; t <= nb; ++t) o.covu = std::min(o.covu, o.cov[t] + o.topk[t]);
-    (void)k;
-    return o;
+    if (dst) std::copy(src.begin(), src.end(), dst);
+}
+
+// validation, ON, q(v), OPT^L and LHGA (host); returns false when ON answers at once
+void inst_prepare(imin_ctx *ctx, Inst &I, const int32_t *S_in, int32_t nS)
+{
+    imin_result *res = I.res;
+    if (!(I.eps > 0.0 && I.eps < 1.0) || !(I.delta > 0.0 && I.delta < 1.0) ||
+        !(I.beta > 0.0 && I.beta < 1.0) || !(I.gamma > 0.0 && I.gamma < 1.0))
+        fail(IMIN_EINVAL, "eps, delta, beta and gamma must lie in (0, 1)");
+    if (I.variant < IMIN_SANDIMIN || I.variant > IMIN_LHGA) fail(IMIN_EINVAL, "unknown variant");
+    const int32_t n = I.g->n, k = I.k;
+    if (k < 1 || (int64_t)k >= (int64_t)n - nS) fail(IMIN_EINVAL, "k must satisfy 1 <= k < n - |S|");
+    std::memset(res, 0, sizeof(*res));
+    res->blockers = I.blockers;
+    res->B_L = I.B_L;
+    res->B_U = I.B_U;
+    res->B_R = I.B_R;
+    prepare_query(ctx, I.g, I.q, S_in, nS, nullptr, 0, true);
+    const imin_graph *g = I.g;
+    const std::vector<int32_t> &S = I.q.S;
+    // ON: out-neighbours of S with p > 0, not in S (Algorithm 4, line 1)
+    std::vector<uint8_t> inON(n, 0);
+    for (int32_t s : S)
+        for (int32_t e = g->h_row_ptr[s]; e < g->h_row_ptr[s + 1]; ++e)
+            if (g->h_thr[e] > 0 && !I.q.is_seed[g->h_col[e]]) inON[g->h_col[e]] = 1;
+    for (int32_t v = 0; v < n; ++v)
+        if (inON[v]) I.ON.push_back(v);
+    I.nVs = (int32_t)I.q.Vs.size();
+    if ((int32_t)I.ON.size() <= k) {   // Algorithm 4, lines 2-3; Sec. 5.3 (nothing sampled)
+        put(I.blockers, I.ON);
+        put(I.B_L, I.ON);
+        put(I.B_U, I.ON);
+        put(I.B_R, I.ON);
+        res->n_blockers = res->nBL = res->nBU = res->nBR = (int32_t)I.ON.size();
+        res->chosen = 0;
+        I.done = true;
+        return;
+    }
+    // q(v) and OPT^L (Sec. 5.1), LHGA scores (Sec. 5.3)
+    std::vector<double> prod(n, 1.0);
+    for (int32_t s : S)
+        for (int32_t e = g->h_row_ptr[s]; e < g->h_row_ptr[s + 1]; ++e) {
+            const int32_t v = g->h_col[e];
+            if (!inON[v]) continue;
+            const double pq = (double)g->h_thr[e] / 16777216.0;
+            prod[v] = prod[v] * (1.0 - pq);
+        }
+    std::vector<ScoreItem> byq(I.ON.size()), bys(I.ON.size());
+    for (size_t i = 0; i < I.ON.size(); ++i) {
+        const int32_t v = I.ON[i];
+        const double qv = 1.0 - prod[v];
+        byq[i] = {qv, v};
+        bys[i] = {qv * (double)(g->h_row_ptr[v + 1] - g->h_row_ptr[v]), v};
+    }
+    std::sort(byq.begin(), byq.end(), score_desc);
+    std::sort(bys.begin(), bys.end(), score_desc);
+    res->nVs = I.nVs;
+    double OPT = 0.0;
+    for (int32_t i = 0; i < k; ++i) OPT += byq[i].score;
+    I.OPT = OPT;
+    res->OPT_L = OPT;
+    I.BRv.resize(k);
+    for (int32_t i = 0; i < k; ++i) I.BRv[i] = bys[i].v;
+    I.do_L = I.variant == IMIN_SANDIMIN || I.variant == IMIN_SANDIMIN_MINUS || I.variant == IMIN_LSBM;
+    I.do_U = I.variant == IMIN_SANDIMIN || I.variant == IMIN_GSBM;
+    I.do_R = I.variant == IMIN_SANDIMIN || I.variant == IMIN_SANDIMIN_MINUS || I.variant == IMIN_LHGA;
+}
+
+// theta_max, theta_0, i_max, a1, a2 of LSBM (Algorithm 4 lines 6-10) or GSBM (Sec. 5.2)
+void bound_init(Inst &I, Bound &B, bool upper)
+{
+    const double a = 1.0 - 1.0 / IM_E;
+    const int32_t n = I.g->n, nS = (int32_t)I.q.S.size(), k = I.k;
+    double th0d;
+    if (!upper) {
+        const double l12 = std::log(12.0 / I.delta);
+        const double c1 = a * std::sqrt(l12) + std::sqrt(a * (ln_binom((double)(n - nS), (double)k) + l12));
+        B.th_max = 2.0 * I.I_hat * c1 * c1 / ((1.0 - I.beta) * I.eps * I.eps * I.OPT);
+        th0d = std::floor(B.th_max * (1.0 - I.beta) * I.eps * I.eps * I.OPT / I.I_hat);
+    } else {
+        const double l6 = std::log(6.0 / I.delta);
+        int32_t top = I.nVs - nS;
+        if (top < k) top = k;
+        const double c2 = a * std::sqrt(l6) + std::sqrt(a * (ln_binom((double)top, (double)k) + l6));
+        B.th_max = 2.0 * (double)I.nVs * c2 * c2 / (I.eps * I.eps * I.OPT);
+        th0d = std::floor(B.th_max * I.eps * I.eps * I.OPT / (double)I.nVs);
+    }
+    if (th0d < 1.0) th0d = 1.0;
+    int32_t imax = (int32_t)std::ceil(std::log2(B.th_max / th0d));
+    if (imax < 1) imax = 1;
+    uint64_t th = (uint64_t)th0d;
+    if (I.fixed_theta) {
+        th = I.fixed_theta;
+        imax = 1;
+    }
+    B.th = th;
+    B.imax = imax;
+    B.a1 = std::log(3.0 * (double)imax / I.delta);
+    B.a2 = B.a1;
+    B.from = 0;
+    B.to = th;
+    B.it = 0;
+    B.active = true;
+}
+
+// sigma^L / sigma^U of one iteration (Algorithm 4 lines 13-19; Sec. 5.2); true = stop
+bool bound_check(Inst &I, Bound &B, bool upper, uint64_t n1, uint64_t n2)
+{
+    const double one_m_inv_e_m_eps = 1.0 - 1.0 / IM_E - I.eps;
+    const unsigned long long cov2 = B.cov2;
+    if (!upper) {
+        const double xlo = (double)cov2 * (1.0 - I.beta) / I.I_hat;
+        const double xhi = (double)cov2 * (1.0 + I.beta) / I.I_hat;
+        B.sL = 0.0;
+        if (xlo >= 5.0 * B.a1 / 18.0)
+            B.sL = sigma_low(xlo, B.a1, (double)n2);
+        else if (xhi <= 5.0 * B.a1 / 18.0)
+            B.sL = sigma_low(xhi, B.a1, (double)n2);
+        B.sU = sigma_up((double)B.go.covu * (1.0 + I.beta) / I.I_hat, B.a2, (double)n1);
+    } else {
+        B.sL = sigma_low((double)cov2, B.a1, (double)n2) * (double)I.nVs;
+        B.sU = sigma_up((double)B.go.covu, B.a2, (double)n1) * (double)I.nVs;
+    }
+    return B.sL / B.sU >= one_m_inv_e_m_eps || B.it == B.imax;
+}
+
+struct Stage {
+    double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double kms[4] = {0, 0, 0, 0};
+};
+
+void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
+{
+    Timer total;
+    const unsigned long long launches0 = g_kernel_launches;
+    Stage stg;
+    GreedyBufs gb;
+    DBuf d_cov;
+    d_cov.ensure(ctx, 16);
+    unsigned long long h_cov = 0;
+    std::vector<Inst *> act;
+    for (Inst *I : all)
+        if (!I->done) act.push_back(I);
+
+    // ---- spread estimates (beta, delta/6): Algorithm 4, line 4 (one launch) ----
+    Timer t0;
+    {
+        std::vector<StopSpec> sp;
+        for (Inst *I : act)
+            sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
+        if (!sp.empty()) stop_rules(ctx, sp);
+        for (size_t i = 0; i < act.size(); ++i) {
+            Inst &I = *act[i];
+            const SpreadEst &e = sp[i].est;
+            I.I_hat = e.I;
+            I.res->I_hat = e.I;
+            I.res->n_spread = e.N;
+            I.res->worlds_sampled += e.worlds;
+            I.res->edges_scanned += e.edges;
+            I.res->reach_nodes += e.nodes;
+            I.res->reach_edges += e.edges;
+            if (i == 0) {
+                stg.kms[0] += e.kernel_ms;
+                I.res->reach_launches += e.launches;
+            }
+        }
+    }
+    stg.ms[0] = t0.ms();
+
+    // ---- LSBM (Algorithm 4) and GSBM (Sec. 5.2), all instances together ----
+    for (int upper = 0; upper < 2; ++upper) {
+        std::vector<Inst *> bl;
+        for (Inst *I : act)
+            if (upper ? I->do_U : I->do_L) {
+                bound_init(*I, upper ? I->U : I->L, upper != 0);
+                const int32_t n = I->g->n;
+                DBuf &cred = upper ? I->credL1 : I->credC1;
+                cred.ensure(ctx, (size_t)n * 8);
+                IM_CUDA(cudaMemsetAsync(cred.p, 0, (size_t)n * 8, ctx->stream));
+                bl.push_back(I);
+            }
+        double samp_ms = 0.0, greedy_ms = 0.0;
+        while (!bl.empty()) {
+            // sampling: append [from, to) to both collections of every active instance
+            Timer ts;
+            if (!upper) {
+                std::vector<CpJob> jobs;
+                for (Inst *I : bl) {
+                    Bound &B = I->L;
+                    const double per_world = std::max(I->I_hat - (double)I->q.S.size(), 1.0);
+                    jobs.push_back(CpJob{I->g, &I->q, &I->C1, 1u, I->credC1.as<unsigned long long>(),
+                                         B.from, B.to, I->key, I->inst, per_world, &B.st});
+                    jobs.push_back(CpJob{I->g, &I->q, &I->C2, 2u, nullptr, B.from, B.to, I->key,
+                                         I->inst, per_world, &B.st});
+                }
+                sample_cp(ctx, jobs);
+            } else {
+                std::vector<LrrJob> jobs;
+                for (Inst *I : bl) {
+                    Bound &B = I->U;
+                    jobs.push_back(LrrJob{I->g, &I->q, &I->L1, 3u, I->credL1.as<unsigned long long>(),
+                                          B.from, B.to, I->key, I->inst, &B.st});
+                    jobs.push_back(LrrJob{I->g, &I->q, &I->L2, 4u, nullptr, B.from, B.to, I->key,
+                                          I->inst, &B.st});
+                }
+                sample_lrr(ctx, jobs);
+            }
+            samp_ms += ts.ms();
+            // Max-Coverage on C1 / L1 of every active instance (one batch)
+            Timer tg;
+            std::vector<GreedyJob> gj(bl.size());
+            std::vector<GreedyJob *> gjp;
+            for (size_t i = 0; i < bl.size(); ++i) {
+                Inst *I = bl[i];
+                gj[i].n = I->g->n;
+                gj[i].k = I->k;
+                if (!upper) {
+                    gj[i].c = &I->C1;
+                    gj[i].credit = I->credC1.as<unsigned long long>();
+                } else {
+                    gj[i].L = &I->L1;
+                    gj[i].credit = I->credL1.as<unsigned long long>();
+                }
+                gjp.push_back(&gj[i]);
+            }
+            const double gk = greedy_batch(ctx, gb, gjp);
+            stg.kms[3] += gk;
+            std::vector<Inst *> next;
+            for (size_t i = 0; i < bl.size(); ++i) {
+                Inst &I = *bl[i];
+                Bound &B = upper ? I.U : I.L;
+                B.go = std::move(gj[i].out);
+                B.it += 1;
+                set_bitmap_host(ctx, I.inB, I.q.words, B.go.B);
+                if (!upper) {
+                    B.cov2 = cov_cp(ctx, I.C2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
+                    if (bound_check(I, B, false, I.C1.worlds, I.C2.worlds)) continue;
+                } else {
+                    B.cov2 = cov_lrr(ctx, I.L2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
+                    if (bound_check(I, B, true, I.L1.nsets, I.L2.nsets)) continue;
+                }
+                // double both collections: worlds [th, 2 th)
+                B.from = B.th;
+                B.to = 2 * B.th;
+                B.th *= 2;
+                next.push_back(&I);
+            }
+            greedy_ms += tg.ms();
+            bl.swap(next);
+        }
+        stg.ms[upper ? 3 : 1] = samp_ms;
+        stg.ms[upper ? 4 : 2] = greedy_ms;
+        for (Inst *I : act) {
+            if (!(upper ? I->do_U : I->do_L)) continue;
+            Bound &B = upper ? I->U : I->L;
+            imin_result *res = I->res;
+            res->worlds_sampled += B.st.worlds;
+            res->edges_scanned += B.st.edges;
+            stg.kms[upper ? 2 : 1] += B.st.kernel_ms;
+            if (!upper) {
+                I->BLv = B.go.B;
+                res->nBL = (int32_t)I->BLv.size();
+                put(I->B_L, I->BLv);
+                res->sigmaL_L = B.sL;
+                res->sigmaU_L = B.sU;
+                res->iters_L = B.it;
+                res->theta_C1 = I->C1.worlds;
+                res->theta_C2 = I->C2.worlds;
+                res->covC2 = B.cov2;
+                res->DL_hat = (double)B.cov2 / (double)I->C2.worlds;
+                res->theta_max_L = B.th_max;
+            } else {
+                I->BUv = B.go.B;
+                res->nBU = (int32_t)I->BUv.size();
+                put(I->B_U, I->BUv);
+                res->sigmaL_U = B.sL;
+                res->sigmaU_U = B.sU;
+                res->iters_U = B.it;
+                res->theta_L1 = I->L1.nsets;
+                res->theta_L2 = I->L2.nsets;
+                res->covL2 = B.cov2;
+                res->DU_hat = (double)I->nVs * (double)B.cov2 / (double)I->L2.nsets;
+                res->theta_max_U = B.th_max;
+            }
+            // the collections are no longer needed
+            if (!upper) {
+                I->C1.release();
+                I->C2.release();
+            } else {
+                I->L1.release();
+                I->L2.release();
+            }
+        }
+    }
+
+    // ---- Sandwich: Algorithm 1, lines 4-5 (one launch for every candidate) ----
+    Timer tf;
+    std::vector<StopSpec> fin;
+    std::vector<std::pair<Inst *, int>> fin_ref;
+    std::vector<std::unique_ptr<Query>> qbs;
+    for (Inst *I : act) {
+        I->res->nBR = I->k;
+        put(I->B_R, I->BRv);
+        const std::vector<int32_t> *cand[3] = {&I->BLv, &I->BUv, &I->BRv};
+        const bool use[3] = {I->do_L, I->do_U, I->do_R};
+        for (int c = 0; c < 3; ++c) {
+            I->res->I_after[c] = 0.0;
+            if (!use[c]) continue;
+            qbs.emplace_back(new Query());
+            prepare_query(ctx, I->g, *qbs.back(), I->q.S.data(), (int32_t)I->q.S.size(),
+                          cand[c]->data(), (int32_t)cand[c]->size(), true);
+            fin.push_back(StopSpec{I->g, qbs.back().get(), I->gamma, I->delta, I->key,
+                                   (uint32_t)(5 + c), I->inst, SpreadEst{}});
+            fin_ref.emplace_back(I, c);
+        }
+    }
+    if (!fin.empty()) stop_rules(ctx, fin);
+    for (size_t i = 0; i < fin.size(); ++i) {
+        Inst &I = *fin_ref[i].first;
+        const int c = fin_ref[i].second;
+        const SpreadEst &e = fin[i].est;
+        imin_result *res = I.res;
+        res->I_after[c] = e.I;
+        res->n_final[c] = e.N;
+        res->worlds_sampled += e.worlds;
+        res->edges_scanned += e.edges;
+        res->reach_nodes += e.nodes;
+        res->reach_edges += e.edges;
+        if (i == 0) {
+            stg.kms[0] += e.kernel_ms;
+            res->reach_launches += e.launches;
+        }
+    }
+    stg.ms[5] = tf.ms();
+    for (Inst *I : act) {
+        imin_result *res = I->res;
+        const std::vector<int32_t> *cand[3] = {&I->BLv, &I->BUv, &I->BRv};
+        const bool use[3] = {I->do_L, I->do_U, I->do_R};
+        int best = -1;
+        for (int c = 0; c < 3; ++c)
+            if (use[c] && (best < 0 || res->I_after[c] < res->I_after[best])) best = c;
+        res->chosen = best;
+        res->n_blockers = (int32_t)cand[best]->size();
+        put(I->blockers, *cand[best]);
+        if (I->do_U && I->variant == IMIN_SANDIMIN && res->DU_hat > 0.0) {
+            const double one_m_inv_e_m_eps = 1.0 - 1.0 / IM_E - I->eps;
+            const double gr = (1.0 - I->gamma) * (1.0 - I->gamma) / ((1.0 + I->gamma) * (1.0 + I->gamma));
+            res->ratio_lb = gr * one_m_inv_e_m_eps * (I->I_hat - res->I_after[1]) / res->DU_hat;
+        }
+    }
+    stg.ms[7] = total.ms();
+    stg.ms[6] = stg.ms[7] - stg.ms[0] - stg.ms[1] - stg.ms[2] - stg.ms[3] - stg.ms[4] - stg.ms[5];
+    // stage times and device times belong to the whole batch: every result reports them
+    for (Inst *I : all) {
+        for (int i = 0; i < 8; ++i) I->res->ms_stage[i] = I->done && act.empty() ? 0.0 : stg.ms[i];
+        for (int i = 0; i < 4; ++i) I->res->kernel_ms[i] = stg.kms[i];
+        I->res->kernel_launches = g_kernel_launches - launches0;
+    }
 }
 
 }  // namespace
@@ -941,293 +1334,49 @@ int imin_solve(imin_graph *g, const int32_t *S_in, int32_t nS, int32_t k, double
                const imin_solve_opts *opts, imin_result *res)
 {
     if (!g || !opts || !res || !res->blockers) return IMIN_EINVAL;
-    imin_ctx *ctx = g->ctx;
+    imin_query q;
+    q.g = g;
+    q.S = S_in;
+    q.nS = nS;
+    q.k = k;
+    q.eps = eps;
+    q.delta = delta;
+    q.opts = *opts;
+    return imin_solve_batch(g->ctx, 1, &q, res);
+}
+
+int imin_solve_batch(imin_ctx *ctx, int32_t n_inst, const imin_query *queries, imin_result *results)
+{
+    if (!ctx || n_inst < 0 || (n_inst > 0 && (!queries || !results))) return IMIN_EINVAL;
+    for (int32_t i = 0; i < n_inst; ++i)
+        if (!queries[i].g || queries[i].g->ctx != ctx || !results[i].blockers) return IMIN_EINVAL;
     return run_guarded(ctx, [&] {
-        Timer total;
-        const unsigned long long launches0 = g_kernel_launches;
         IM_CUDA(cudaSetDevice(ctx->device));
-        const double beta = opts->beta, gamma = opts->gamma;
-        if (!(eps > 0.0 && eps < 1.0) || !(delta > 0.0 && delta < 1.0) || !(beta > 0.0 && beta < 1.0) ||
-            !(gamma > 0.0 && gamma < 1.0))
-            fail(IMIN_EINVAL, "eps, delta, beta and gamma must lie in (0, 1)");
-        if (opts->variant < IMIN_SANDIMIN || opts->variant > IMIN_LHGA) fail(IMIN_EINVAL, "unknown variant");
-        const int32_t n = g->n;
-        if (k < 1 || (int64_t)k >= (int64_t)n - nS) fail(IMIN_EINVAL, "k must satisfy 1 <= k < n - |S|");
-        const uint64_t key = opts->key;
-        const uint32_t inst = opts->inst;
-        const int variant = opts->variant;
-        int32_t *B_L = res->B_L, *B_U = res->B_U, *B_R = res->B_R, *blockers = res->blockers;
-        std::memset(res, 0, sizeof(*res));
-        res->blockers = blockers;
-        res->B_L = B_L;
-        res->B_U = B_U;
-        res->B_R = B_R;
-
-        Query q;
-        prepare_query(ctx, g, q, S_in, nS, nullptr, 0, true);
-        const std::vector<int32_t> &S = q.S;
-        Timer host_t;
-        double host_ms = 0.0;
-
-        // ON: out-neighbours of S with p > 0, not in S (Algorithm 4, line 1)
-        std::vector<uint8_t> inON(n, 0);
-        for (int32_t s : S)
-            for (int32_t e = g->h_row_ptr[s]; e < g->h_row_ptr[s + 1]; ++e)
-                if (g->h_thr[e] > 0 && !q.is_seed[g->h_col[e]]) inON[g->h_col[e]] = 1;
-        std::vector<int32_t> ON;
-        for (int32_t v = 0; v < n; ++v)
-            if (inON[v]) ON.push_back(v);
-        auto put = [&](int32_t *dst, const std::vector<int32_t> &src) {
-            if (dst) std::copy(src.begin(), src.end(), dst);
-        };
-        if ((int32_t)ON.size() <= k) {   // Algorithm 4, lines 2-3; Sec. 5.3
-            put(blockers, ON);
-            put(B_L, ON);
-            put(B_U, ON);
-            put(B_R, ON);
-            res->n_blockers = res->nBL = res->nBU = res->nBR = (int32_t)ON.size();
-            res->chosen = 0;
-            res->nVs = (int32_t)q.Vs.size();
-            res->ms_stage[7] = total.ms();
-            return;
+        std::vector<std::unique_ptr<Inst>> owned;
+        std::vector<Inst *> all;
+        for (int32_t i = 0; i < n_inst; ++i) {
+            const imin_query &qq = queries[i];
+            owned.emplace_back(new Inst());
+            Inst &I = *owned.back();
+            I.g = qq.g;
+            I.k = qq.k;
+            I.eps = qq.eps;
+            I.delta = qq.delta;
+            I.beta = qq.opts.beta;
+            I.gamma = qq.opts.gamma;
+            I.key = qq.opts.key;
+            I.inst = qq.opts.inst;
+            I.variant = qq.opts.variant;
+            I.fixed_theta = qq.opts.fixed_theta;
+            I.res = &results[i];
+            I.blockers = results[i].blockers;
+            I.B_L = results[i].B_L;
+            I.B_U = results[i].B_U;
+            I.B_R = results[i].B_R;
+            inst_prepare(ctx, I, qq.S, qq.nS);
+            all.push_back(&I);
         }
-        // q(v) and OPT^L (Sec. 5.1), LHGA scores (Sec. 5.3)
-        std::vector<double> prod(n, 1.0);
-        for (int32_t s : S)
-            for (int32_t e = g->h_row_ptr[s]; e < g->h_row_ptr[s + 1]; ++e) {
-                const int32_t v = g->h_col[e];
-                if (!inON[v]) continue;
-                const double pq = (double)g->h_thr[e] / 16777216.0;
-                prod[v] = prod[v] * (1.0 - pq);
-            }
-        std::vector<ScoreItem> byq(ON.size()), bys(ON.size());
-        for (size_t i = 0; i < ON.size(); ++i) {
-            const int32_t v = ON[i];
-            const double qv = 1.0 - prod[v];
-            byq[i] = {qv, v};
-            bys[i] = {qv * (double)(g->h_row_ptr[v + 1] - g->h_row_ptr[v]), v};
-        }
-        std::sort(byq.begin(), byq.end(), score_desc);
-        std::sort(bys.begin(), bys.end(), score_desc);
-        double OPT = 0.0;
-        for (int32_t i = 0; i < k; ++i) OPT += byq[i].score;
-        res->OPT_L = OPT;
-        std::vector<int32_t> BRv(k);
-        for (int32_t i = 0; i < k; ++i) BRv[i] = bys[i].v;
-        const int32_t nVs = (int32_t)q.Vs.size();
-        res->nVs = nVs;
-        const double one_m_inv_e_m_eps = 1.0 - 1.0 / IM_E - eps;
-        host_ms += host_t.ms();
-
-        const bool do_L = variant == IMIN_SANDIMIN || variant == IMIN_SANDIMIN_MINUS || variant == IMIN_LSBM;
-        const bool do_U = variant == IMIN_SANDIMIN || variant == IMIN_GSBM;
-        const bool do_R = variant == IMIN_SANDIMIN || variant == IMIN_SANDIMIN_MINUS || variant == IMIN_LHGA;
-        const size_t words = q.words;
-        DBuf d_inB, d_cov;
-        d_cov.ensure(ctx, 16);
-        unsigned long long h_cov = 0;
-        GreedyBufs gb;
-        std::vector<int32_t> BLv, BUv;
-
-        // ---- spread estimate (beta, delta/6): Algorithm 4, line 4 ----
-        Timer t0;
-        SpreadEst I0 = stop_rule(ctx, g, q, beta, delta / 6.0, key, 0, inst);
-        const double I_hat = I0.I;
-        res->I_hat = I_hat;
-        res->n_spread = I0.N;
-        res->worlds_sampled += I0.worlds;
-        res->edges_scanned += I0.edges;
-        res->kernel_ms[0] += I0.kernel_ms;
-        res->reach_nodes += I0.nodes;
-        res->reach_edges += I0.edges;
-        res->reach_launches += I0.launches;
-        res->ms_stage[0] = t0.ms();
-
-        // ---- LSBM (Algorithm 4) ----
-        if (do_L) {
-            Timer ts;
-            const double a = 1.0 - 1.0 / IM_E;
-            const double l12 = std::log(12.0 / delta);
-            const double c1 = a * std::sqrt(l12) + std::sqrt(a * (ln_binom((double)(n - nS), (double)k) + l12));
-            const double th_max = 2.0 * I_hat * c1 * c1 / ((1.0 - beta) * eps * eps * OPT);
-            double th0d = std::floor(th_max * (1.0 - beta) * eps * eps * OPT / I_hat);
-            if (th0d < 1.0) th0d = 1.0;
-            int32_t imax = (int32_t)std::ceil(std::log2(th_max / th0d));
-            if (imax < 1) imax = 1;
-            uint64_t th = (uint64_t)th0d;
-            if (opts->fixed_theta) {
-                th = opts->fixed_theta;
-                imax = 1;
-            }
-            res->theta_max_L = th_max;
-            const double a1 = std::log(3.0 * (double)imax / delta), a2 = a1;
-            CpStore C1, C2;
-            DBuf credC1;
-            credC1.ensure(ctx, (size_t)n * 8);
-            IM_CUDA(cudaMemsetAsync(credC1.p, 0, (size_t)n * 8, ctx->stream));
-            const double per_world = std::max(I_hat - (double)nS, 1.0);
-            SpreadEst st;
-            std::vector<CpJob> cj{CpJob{&C1, 1u, credC1.as<unsigned long long>()},
-                                  CpJob{&C2, 2u, nullptr}};
-            sample_cp(ctx, g, q, cj, 0, th, key, inst, per_world, &st);
-            double samp_ms = ts.ms(), greedy_ms = 0.0;
-            GreedyOut go;
-            double sL = 0.0, sU = 0.0;
-            unsigned long long cov2 = 0;
-            for (int32_t i = 1; i <= imax; ++i) {
-                Timer tg;
-                {
-                    EventTimer et(ctx);
-                    greedy_cp(ctx, gb, C1, n, k, credC1.as<unsigned long long>());
-                    res->kernel_ms[3] += et.stop();
-                }
-                go = read_greedy(ctx, gb, k);
-                set_bitmap_host(ctx, d_inB, words, go.B);
-                cov2 = cov_cp(ctx, C2, d_inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
-                greedy_ms += tg.ms();
-                const double xlo = (double)cov2 * (1.0 - beta) / I_hat;
-                const double xhi = (double)cov2 * (1.0 + beta) / I_hat;
-                sL = 0.0;
-                if (xlo >= 5.0 * a1 / 18.0)
-                    sL = sigma_low(xlo, a1, (double)C2.worlds);
-                else if (xhi <= 5.0 * a1 / 18.0)
-                    sL = sigma_low(xhi, a1, (double)C2.worlds);
-                sU = sigma_up((double)go.covu * (1.0 + beta) / I_hat, a2, (double)C1.worlds);
-                res->iters_L = i;
-                if (sL / sU >= one_m_inv_e_m_eps || i == imax) break;
-                Timer ts2;
-                sample_cp(ctx, g, q, cj, th, 2 * th, key, inst, per_world, &st);
-                samp_ms += ts2.ms();
-                th *= 2;
-            }
-            BLv = go.B;
-            res->nBL = (int32_t)BLv.size();
-            put(B_L, BLv);
-            res->sigmaL_L = sL;
-            res->sigmaU_L = sU;
-            res->theta_C1 = C1.worlds;
-            res->theta_C2 = C2.worlds;
-            res->covC2 = cov2;
-            res->DL_hat = (double)cov2 / (double)C2.worlds;
-            res->ms_stage[1] = samp_ms;
-            res->ms_stage[2] = greedy_ms;
-            res->worlds_sampled += st.worlds;
-            res->edges_scanned += st.edges;
-            res->kernel_ms[1] += st.kernel_ms;
-        }
-
-        // ---- GSBM (Sec. 5.2) ----
-        if (do_U) {
-            Timer ts;
-            const double a = 1.0 - 1.0 / IM_E;
-            const double l6 = std::log(6.0 / delta);
-            int32_t top = nVs - nS;
-            if (top < k) top = k;
-            const double c2 = a * std::sqrt(l6) + std::sqrt(a * (ln_binom((double)top, (double)k) + l6));
-            const double th_max = 2.0 * (double)nVs * c2 * c2 / (eps * eps * OPT);
-            double th0d = std::floor(th_max * eps * eps * OPT / (double)nVs);
-            if (th0d < 1.0) th0d = 1.0;
-            int32_t imax = (int32_t)std::ceil(std::log2(th_max / th0d));
-            if (imax < 1) imax = 1;
-            uint64_t th = (uint64_t)th0d;
-            if (opts->fixed_theta) {
-                th = opts->fixed_theta;
-                imax = 1;
-            }
-            res->theta_max_U = th_max;
-            const double a1 = std::log(3.0 * (double)imax / delta), a2 = a1;
-            LrrStore L1, L2;
-            DBuf credL1;
-            credL1.ensure(ctx, (size_t)n * 8);
-            IM_CUDA(cudaMemsetAsync(credL1.p, 0, (size_t)n * 8, ctx->stream));
-            SpreadEst st;
-            std::vector<LrrJob> lj{LrrJob{&L1, 3u, credL1.as<unsigned long long>()},
-                                   LrrJob{&L2, 4u, nullptr}};
-            sample_lrr(ctx, g, q, lj, 0, th, key, inst, &st);
-            double samp_ms = ts.ms(), greedy_ms = 0.0;
-            GreedyOut go;
-            double sL = 0.0, sU = 0.0;
-            unsigned long long cov2 = 0;
-            for (int32_t i = 1; i <= imax; ++i) {
-                Timer tg;
-                {
-                    EventTimer et(ctx);
-                    greedy_lrr(ctx, gb, L1, n, k, credL1.as<unsigned long long>());
-                    res->kernel_ms[3] += et.stop();
-                }
-                go = read_greedy(ctx, gb, k);
-                set_bitmap_host(ctx, d_inB, words, go.B);
-                cov2 = cov_lrr(ctx, L2, d_inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
-                greedy_ms += tg.ms();
-                sL = sigma_low((double)cov2, a1, (double)L2.nsets) * (double)nVs;
-                sU = sigma_up((double)go.covu, a2, (double)L1.nsets) * (double)nVs;
-                res->iters_U = i;
-                if (sL / sU >= one_m_inv_e_m_eps || i == imax) break;
-                Timer ts2;
-                sample_lrr(ctx, g, q, lj, th, 2 * th, key, inst, &st);
-                samp_ms += ts2.ms();
-                th *= 2;
-            }
-            BUv = go.B;
-            res->nBU = (int32_t)BUv.size();
-            put(B_U, BUv);
-            res->sigmaL_U = sL;
-            res->sigmaU_U = sU;
-            res->theta_L1 = L1.nsets;
-            res->theta_L2 = L2.nsets;
-            res->covL2 = cov2;
-            res->DU_hat = (double)nVs * (double)cov2 / (double)L2.nsets;
-            res->ms_stage[3] = samp_ms;
-            res->ms_stage[4] = greedy_ms;
-            res->worlds_sampled += st.worlds;
-            res->edges_scanned += st.edges;
-            res->kernel_ms[2] += st.kernel_ms;
-        }
-        res->nBR = k;
-        put(B_R, BRv);
-
-        // ---- Sandwich: Algorithm 1, lines 4-5 ----
-        Timer tf;
-        const std::vector<int32_t> *cand[3] = {&BLv, &BUv, &BRv};
-        const bool use[3] = {do_L, do_U, do_R};
-        Query qb[3];
-        std::vector<StopSpec> fin;
-        std::vector<int> fin_c;
-        for (int c = 0; c < 3; ++c) {
-            res->I_after[c] = 0.0;
-            if (!use[c]) continue;
-            prepare_query(ctx, g, qb[c], S.data(), (int32_t)S.size(), cand[c]->data(),
-                          (int32_t)cand[c]->size(), true);
-            fin.push_back(StopSpec{g, &qb[c], gamma, delta, key, (uint32_t)(5 + c), inst, SpreadEst{}});
-            fin_c.push_back(c);
-        }
-        stop_rules(ctx, fin);
-        int best = -1;
-        for (size_t i = 0; i < fin.size(); ++i) {
-            const int c = fin_c[i];
-            const SpreadEst &e = fin[i].est;
-            res->I_after[c] = e.I;
-            res->n_final[c] = e.N;
-            res->worlds_sampled += e.worlds;
-            res->edges_scanned += e.edges;
-            res->kernel_ms[0] += e.kernel_ms;
-            res->reach_nodes += e.nodes;
-            res->reach_edges += e.edges;
-            res->reach_launches += e.launches;
-        }
-        for (int c = 0; c < 3; ++c)
-            if (use[c] && (best < 0 || res->I_after[c] < res->I_after[best])) best = c;
-        res->ms_stage[5] = tf.ms();
-        res->chosen = best;
-        res->n_blockers = (int32_t)cand[best]->size();
-        put(blockers, *cand[best]);
-        if (do_U && variant == IMIN_SANDIMIN && res->DU_hat > 0.0) {
-            const double gr = (1.0 - gamma) * (1.0 - gamma) / ((1.0 + gamma) * (1.0 + gamma));
-            res->ratio_lb = gr * one_m_inv_e_m_eps * (I_hat - res->I_after[1]) / res->DU_hat;
-        }
-        res->ms_stage[6] = host_ms;
-        res->ms_stage[7] = total.ms();
-        res->kernel_launches = g_kernel_launches - launches0;
+        solve_all(ctx, all);
     });
 }
 

@@ -30,19 +30,25 @@ __device__ __forceinline__ bool better(unsigned long long g1, int v1, unsigned l
     return g1 > g2 || (g1 == g2 && v1 < v2);
 }
 
-// per-block argmax -> partials; the last block reduces, commits the pick, and
-// initialises the top-k selection for this round.
-__global__ void __launch_bounds__(256) k_argmax(GState *st, const unsigned long long *gain, int32_t n,
-                                                unsigned long long *part_g, int32_t *part_v,
-                                                unsigned int *done_ctr, int32_t round, int32_t k,
-                                                int32_t *B, unsigned long long *cov)
+// Every kernel below serves all instances of a batch: a table maps each block to its
+// instance, so one launch per round step covers every Max-Coverage run at once.
+
+// per-block argmax -> partials; the instance's last block reduces, commits the pick
+// and initialises the top-k selection of this round
+__global__ void __launch_bounds__(256) k_argmax(const GInst *gi, const int32_t *blk2inst,
+                                                int32_t round)
 {
+    const GInst &I = gi[blk2inst[blockIdx.x]];
+    if (round > I.k) return;
+    GState *st = I.st;
     if (st->stopped) return;
+    const int lb = (int)blockIdx.x - I.blk0;
+    const int32_t n = I.n;
     unsigned long long bg = 0;
     int bv = 0x7fffffff;
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long gv = gain[v];
+    for (int64_t v = (int64_t)lb * blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)I.nblk * blockDim.x) {
+        const unsigned long long gv = I.gain[v];
         if (better(gv, (int)v, bg, bv)) {
             bg = gv;
             bv = (int)v;
@@ -72,47 +78,47 @@ __global__ void __launch_bounds__(256) k_argmax(GState *st, const unsigned long 
                 bg = sg[i];
                 bv = sv[i];
             }
-        part_g[blockIdx.x] = bg;
-        part_v[blockIdx.x] = bv;
+        I.part_g[lb] = bg;
+        I.part_v[lb] = bv;
         __threadfence();
-        const unsigned int t = atomicAdd(done_ctr, 1u);
-        last = (t == gridDim.x - 1);
+        const unsigned int t = atomicAdd(I.done_ctr, 1u);
+        last = (t == (unsigned)I.nblk - 1);
     }
     __syncthreads();
     if (!last || threadIdx.x != 0) return;
     __threadfence();
     bg = 0;
     bv = 0x7fffffff;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-        const unsigned long long g = *(volatile unsigned long long *)(part_g + b);
-        const int v = *(volatile int *)(part_v + b);
+    for (int b = 0; b < I.nblk; ++b) {
+        const unsigned long long g = *(volatile unsigned long long *)(I.part_g + b);
+        const int v = *(volatile int *)(I.part_v + b);
         if (better(g, v, bg, bv)) {
             bg = g;
             bv = v;
         }
     }
-    *done_ctr = 0;
+    *I.done_ctr = 0;
     st->gmax = bg;
     st->u = bv;
     st->pick = 0;
-    // top-k selection state for this round
     st->tsum = 0;
-    st->krem = k < n ? k : n;
+    st->krem = I.k < n ? I.k : n;
     st->prefix = 0;
     if (bg == 0) {
         st->hi = 0;
         st->tdone = 1;
+        I.topk[round] = 0;            // every gain is 0
     } else {
         st->hi = 64 - __clzll((long long)bg);
         st->tdone = 0;
     }
-    if (round < k) {
+    if (round < I.k) {
         if (bg == 0) {
             st->stopped = 1;          // nothing left to cover: |B| = round
             st->nb = round;
         } else {
-            B[round] = bv;
-            cov[round + 1] = cov[round] + bg;
+            I.B[round] = bv;
+            I.cov[round + 1] = I.cov[round] + bg;
             st->pick = 1;
             st->nb = round + 1;
         }
@@ -120,11 +126,14 @@ __global__ void __launch_bounds__(256) k_argmax(GState *st, const unsigned long 
 }
 
 // histogram of the next digit of the gains that match the selected prefix
-__global__ void __launch_bounds__(256) k_topk_hist(const GState *st, const unsigned long long *gain,
-                                                   int32_t n, unsigned int *hcnt,
-                                                   unsigned long long *hsum)
+__global__ void __launch_bounds__(256) k_topk_hist(const GInst *gi, const int32_t *blk2inst,
+                                                   int32_t round)
 {
+    const GInst &I = gi[blk2inst[blockIdx.x]];
+    if (round > I.k) return;
+    const GState *st = I.st;
     if (st->tdone) return;
+    const int lb = (int)blockIdx.x - I.blk0;
     const int hi = st->hi;
     const int lo = hi > RS_BITS ? hi - RS_BITS : 0;
     const unsigned long long prefix = st->prefix;
@@ -136,9 +145,9 @@ __global__ void __launch_bounds__(256) k_topk_hist(const GState *st, const unsig
         ss[i] = 0;
     }
     __syncthreads();
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long g = gain[v];
+    for (int64_t v = (int64_t)lb * blockDim.x + threadIdx.x; v < I.n;
+         v += (int64_t)I.nblk * blockDim.x) {
+        const unsigned long long g = I.gain[v];
         if (hi < 64 && (g >> hi) != (prefix >> hi)) continue;
         const int d = (int)((g >> lo) & dmask);
         atomicAdd(&sc[d], 1u);
@@ -147,24 +156,26 @@ __global__ void __launch_bounds__(256) k_topk_hist(const GState *st, const unsig
     __syncthreads();
     for (int i = threadIdx.x; i < RS_BINS; i += blockDim.x)
         if (sc[i]) {
-            atomicAdd(hcnt + i, sc[i]);
-            atomicAdd(hsum + i, ss[i]);
+            atomicAdd(I.hcnt + i, sc[i]);
+            atomicAdd(I.hsum + i, ss[i]);
         }
 }
 
-// pick the digit that holds the k-th largest value; resolve when all bits are fixed
-__global__ void __launch_bounds__(1024) k_topk_select(GState *st, unsigned int *hcnt,
-                                                      unsigned long long *hsum,
-                                                      unsigned long long *topk, int32_t round)
+// one block per instance: pick the digit that holds the k-th largest value;
+// resolve when all bits are fixed
+__global__ void __launch_bounds__(1024) k_topk_select(const GInst *gi, int32_t round)
 {
+    const GInst &I = gi[blockIdx.x];
+    if (round > I.k) return;
+    GState *st = I.st;
     if (st->tdone) return;
     __shared__ unsigned int c[RS_BINS];
     __shared__ unsigned long long s[RS_BINS];
     for (int i = threadIdx.x; i < RS_BINS; i += blockDim.x) {
-        c[i] = hcnt[i];
-        s[i] = hsum[i];
-        hcnt[i] = 0;
-        hsum[i] = 0;
+        c[i] = I.hcnt[i];
+        s[i] = I.hsum[i];
+        I.hcnt[i] = 0;
+        I.hsum[i] = 0;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -185,7 +196,7 @@ __global__ void __launch_bounds__(1024) k_topk_select(GState *st, unsigned int *
     if (dstar < 0) {             // fewer candidates than k: the sum of all of them
         st->tsum = tsum;
         st->tdone = 1;
-        topk[round] = tsum;
+        I.topk[round] = tsum;
         return;
     }
     const unsigned long long prefix = st->prefix | ((unsigned long long)dstar << lo);
@@ -193,7 +204,7 @@ __global__ void __launch_bounds__(1024) k_topk_select(GState *st, unsigned int *
         tsum += (unsigned long long)krem * prefix;
         st->tsum = tsum;
         st->tdone = 1;
-        topk[round] = tsum;
+        I.topk[round] = tsum;
         return;
     }
     st->prefix = prefix;
@@ -202,73 +213,55 @@ __global__ void __launch_bounds__(1024) k_topk_select(GState *st, unsigned int *
     st->tsum = tsum;
 }
 
-__global__ void k_topk_zero(const GState *st, unsigned long long *topk, int32_t round)
+// Decrement after a pick: one warp per record (CP) or set (LRR) of u.
+__global__ void __launch_bounds__(256) k_update(const GInst *gi, const int32_t *ublk2inst,
+                                                int32_t round, int lrr)
 {
-    // gmax == 0: the top-k sum is 0
-    if (st->tdone && st->tsum == 0 && st->gmax == 0) topk[round] = 0;
-}
-
-// Decrement for a pick on CP records: one warp per record of u.
-__global__ void __launch_bounds__(256) k_cp_update(const GState *st, const long long *inv_off,
-                                                   const long long *inv_rec,
-                                                   const int32_t *rnode, const int32_t *rpar,
-                                                   const int32_t *rsize, int32_t *contrib,
-                                                   uint8_t *covered, unsigned long long *gain)
-{
+    const GInst &I = gi[ublk2inst[blockIdx.x]];
+    if (round >= I.k) return;
+    const GState *st = I.st;
     if (!st->pick) return;
     const int u = st->u;
-    const long long beg = inv_off[u], end = inv_off[u + 1];
+    const long long beg = I.inv_off[u], end = I.inv_off[u + 1];
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long idx = beg + gw; idx < end; idx += nw) {
-        const long long r = inv_rec[idx];
-        if (covered[r]) continue;
-        const int newcov = contrib[r];
-        if (lane == 0) {
-            long long x = r;
-            int po = rpar[x];
-            while (po != 0) {
-                x -= po;
-                contrib[x] -= newcov;
-                atomicAdd(gain + rnode[x], (unsigned long long)(-(long long)newcov));
-                po = rpar[x];
+    const long long gw = ((long long)((int)blockIdx.x - I.ublk0) * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)I.unblk * blockDim.x) >> 5;
+    unsigned long long *gain = I.gain;
+    if (!lrr) {
+        for (long long idx = beg + gw; idx < end; idx += nw) {
+            const long long r = I.inv_rec[idx];
+            if (I.covered[r]) continue;
+            const int newcov = I.contrib[r];
+            if (lane == 0) {
+                long long x = r;
+                int po = I.rpar[x];
+                while (po != 0) {
+                    x -= po;
+                    I.contrib[x] -= newcov;
+                    atomicAdd(gain + I.rnode[x], (unsigned long long)(-(long long)newcov));
+                    po = I.rpar[x];
+                }
             }
+            const long long e = r + I.rsize[r];
+            for (long long x = r + lane; x < e; x += 32) {
+                if (I.covered[x]) continue;
+                const int c = I.contrib[x];
+                if (c) atomicAdd(gain + I.rnode[x], (unsigned long long)(-(long long)c));
+                I.contrib[x] = 0;
+                I.covered[x] = 1;
+            }
+            __syncwarp();
         }
-        const long long e = r + rsize[r];
-        for (long long x = r + lane; x < e; x += 32) {
-            if (covered[x]) continue;
-            const int c = contrib[x];
-            if (c) atomicAdd(gain + rnode[x], (unsigned long long)(-(long long)c));
-            contrib[x] = 0;
-            covered[x] = 1;
+    } else {
+        for (long long idx = beg + gw; idx < end; idx += nw) {
+            const uint32_t s = I.inv_set[idx];
+            if (I.covered[s]) continue;
+            const unsigned long long o = I.set_off[s];
+            const uint32_t L = I.set_len[s];
+            for (uint32_t t = lane; t < L; t += 32) atomicAdd(gain + I.set_elem[o + t], ~0ull);
+            __syncwarp();
+            if (lane == 0) I.covered[s] = 1;
         }
-        __syncwarp();
-    }
-}
-
-// Decrement for a pick on LRR sets: one warp per set of u.
-__global__ void __launch_bounds__(256) k_lrr_update(const GState *st, const long long *inv_off,
-                                                    const uint32_t *inv_set,
-                                                    const unsigned long long *set_off,
-                                                    const uint32_t *set_len,
-                                                    const int32_t *set_elem, uint8_t *covered,
-                                                    unsigned long long *gain)
-{
-    if (!st->pick) return;
-    const int u = st->u;
-    const long long beg = inv_off[u], end = inv_off[u + 1];
-    const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long idx = beg + gw; idx < end; idx += nw) {
-        const uint32_t s = inv_set[idx];
-        if (covered[s]) continue;
-        const unsigned long long o = set_off[s];
-        const uint32_t L = set_len[s];
-        for (uint32_t t = lane; t < L; t += 32) atomicAdd(gain + set_elem[o + t], ~0ull);
-        __syncwarp();
-        if (lane == 0) covered[s] = 1;
     }
 }
 
@@ -379,130 +372,199 @@ static int grid_for(imin_ctx *ctx, long long work, int per_block = 256)
     return (int)b;
 }
 
-void greedy_scratch(imin_ctx *ctx, GreedyBufs &gb, int32_t n, int32_t k)
+// inverted index node -> records (CP) or sets (LRR), and the per-run greedy state
+static void prepare_index(imin_ctx *ctx, GreedyJob &j)
 {
-    const int parts = ctx->num_sms * 8;
-    gb.state.ensure(ctx, sizeof(GState));
-    gb.part_g.ensure(ctx, (size_t)parts * 8);
-    gb.part_v.ensure(ctx, (size_t)parts * 4);
-    gb.done.ensure(ctx, 64);
-    gb.hcnt.ensure(ctx, RS_BINS * 4);
-    gb.hsum.ensure(ctx, RS_BINS * 8);
-    gb.B.ensure(ctx, (size_t)(k + 1) * 4);
-    gb.cov.ensure(ctx, (size_t)(k + 2) * 8);
-    gb.topk.ensure(ctx, (size_t)(k + 2) * 8);
-    gb.gain.ensure(ctx, (size_t)n * 8);
-    IM_CUDA(cudaMemsetAsync(gb.done.p, 0, 64, ctx->stream));
-    IM_CUDA(cudaMemsetAsync(gb.hcnt.p, 0, RS_BINS * 4, ctx->stream));
-    IM_CUDA(cudaMemsetAsync(gb.hsum.p, 0, RS_BINS * 8, ctx->stream));
-    IM_CUDA(cudaMemsetAsync(gb.state.p, 0, sizeof(GState), ctx->stream));
-    IM_CUDA(cudaMemsetAsync(gb.cov.p, 0, (size_t)(k + 2) * 8, ctx->stream));
-    IM_CUDA(cudaMemsetAsync(gb.topk.p, 0, (size_t)(k + 2) * 8, ctx->stream));
-}
-
-// k + 1 rounds of argmax / top-k / decrement.  `update` launches the decrement.
-template <class F>
-static void greedy_rounds(imin_ctx *ctx, GreedyBufs &gb, int32_t n, int32_t k, F update)
-{
-    const int grid = grid_for(ctx, n);
-    GState *st = gb.state.as<GState>();
-    for (int32_t round = 0; round <= k; ++round) {
-        k_argmax<<<grid, 256, 0, ctx->stream>>>(st, gb.gain.as<unsigned long long>(), n,
-                                                gb.part_g.as<unsigned long long>(),
-                                                gb.part_v.as<int32_t>(), gb.done.as<unsigned int>(),
-                                                round, k, gb.B.as<int32_t>(),
-                                                gb.cov.as<unsigned long long>());
-        IM_CHECK_LAUNCH();
-        for (int pass = 0; pass < 6; ++pass) {
-            k_topk_hist<<<grid, 256, 0, ctx->stream>>>(st, gb.gain.as<unsigned long long>(), n,
-                                                       gb.hcnt.as<unsigned int>(),
-                                                       gb.hsum.as<unsigned long long>());
-            IM_CHECK_LAUNCH();
-            k_topk_select<<<1, 1024, 0, ctx->stream>>>(st, gb.hcnt.as<unsigned int>(),
-                                                       gb.hsum.as<unsigned long long>(),
-                                                       gb.topk.as<unsigned long long>(), round);
+    cudaStream_t s = ctx->stream;
+    const int32_t n = j.n;
+    if (j.c) {
+        CpStore &c = *j.c;
+        const long long R = c.count;
+        c.inv_off.ensure(ctx, (size_t)(n + 1) * 8);
+        c.inv_rec.ensure(ctx, (size_t)std::max<long long>(R, 1) * 8);
+        c.fill.ensure(ctx, (size_t)(n + 1) * 4);
+        c.contrib.ensure(ctx, (size_t)std::max<long long>(R, 1) * 4);
+        c.covered.ensure(ctx, (size_t)std::max<long long>(R, 1));
+        c.scan_tmp.ensure(ctx, scan_tmp_bytes(n + 1));
+        IM_CUDA(cudaMemsetAsync(c.inv_off.p, 0, (size_t)(n + 1) * 8, s));
+        IM_CUDA(cudaMemsetAsync(c.fill.p, 0, (size_t)(n + 1) * 4, s));
+        if (R > 0) {
+            k_count_nodes<<<grid_for(ctx, R), 256, 0, s>>>(c.node.as<int32_t>(), R, c.inv_off.as<long long>());
             IM_CHECK_LAUNCH();
         }
-        k_topk_zero<<<1, 1, 0, ctx->stream>>>(st, gb.topk.as<unsigned long long>(), round);
-        IM_CHECK_LAUNCH();
-        if (round < k) update();
+        exclusive_scan_i64(ctx, c.inv_off.as<long long>(), n + 1, c.scan_tmp.p);
+        if (R > 0) {
+            k_fill_cp_inv<<<grid_for(ctx, R), 256, 0, s>>>(c.node.as<int32_t>(), R, c.inv_off.as<long long>(),
+                                                          c.fill.as<unsigned int>(), c.inv_rec.as<long long>());
+            IM_CHECK_LAUNCH();
+            k_init_cp<<<grid_for(ctx, R), 256, 0, s>>>(c.size.as<int32_t>(), R, c.contrib.as<int32_t>(),
+                                                      c.covered.as<uint8_t>());
+            IM_CHECK_LAUNCH();
+        }
+    } else {
+        LrrStore &L = *j.L;
+        const long long E = (long long)L.elems;
+        const uint32_t ns = L.nsets;
+        L.inv_off.ensure(ctx, (size_t)(n + 1) * 8);
+        L.inv_set.ensure(ctx, (size_t)std::max<long long>(E, 1) * 4);
+        L.fill.ensure(ctx, (size_t)(n + 1) * 4);
+        L.covered.ensure(ctx, (size_t)std::max<uint32_t>(ns, 1));
+        L.scan_tmp.ensure(ctx, scan_tmp_bytes(n + 1));
+        IM_CUDA(cudaMemsetAsync(L.inv_off.p, 0, (size_t)(n + 1) * 8, s));
+        IM_CUDA(cudaMemsetAsync(L.fill.p, 0, (size_t)(n + 1) * 4, s));
+        IM_CUDA(cudaMemsetAsync(L.covered.p, 0, (size_t)std::max<uint32_t>(ns, 1), s));
+        if (E > 0) {
+            k_count_nodes<<<grid_for(ctx, E), 256, 0, s>>>(L.elem.as<int32_t>(), E, L.inv_off.as<long long>());
+            IM_CHECK_LAUNCH();
+        }
+        exclusive_scan_i64(ctx, L.inv_off.as<long long>(), n + 1, L.scan_tmp.p);
+        if (ns > 0) {
+            k_fill_lrr_inv<<<grid_for(ctx, (long long)ns * 32), 256, 0, s>>>(
+                L.off.as<unsigned long long>(), L.len.as<uint32_t>(), ns, L.elem.as<int32_t>(),
+                L.inv_off.as<long long>(), L.fill.as<unsigned int>(), L.inv_set.as<uint32_t>());
+            IM_CHECK_LAUNCH();
+        }
     }
 }
 
-void greedy_cp(imin_ctx *ctx, GreedyBufs &gb, CpStore &c, int32_t n, int32_t k,
-               const unsigned long long *credit)
-{
-    cudaStream_t s = ctx->stream;
-    const long long R = c.count;
-    // inverted index node -> records
-    c.inv_off.ensure(ctx, (size_t)(n + 1) * 8);
-    c.inv_rec.ensure(ctx, (size_t)std::max<long long>(R, 1) * 8);
-    c.fill.ensure(ctx, (size_t)(n + 1) * 4);
-    c.contrib.ensure(ctx, (size_t)std::max<long long>(R, 1) * 4);
-    c.covered.ensure(ctx, (size_t)std::max<long long>(R, 1));
-    c.scan_tmp.ensure(ctx, scan_tmp_bytes(n + 1));
-    IM_CUDA(cudaMemsetAsync(c.inv_off.p, 0, (size_t)(n + 1) * 8, s));
-    IM_CUDA(cudaMemsetAsync(c.fill.p, 0, (size_t)(n + 1) * 4, s));
-    if (R > 0) {
-        k_count_nodes<<<grid_for(ctx, R), 256, 0, s>>>(c.node.as<int32_t>(), R, c.inv_off.as<long long>());
-        IM_CHECK_LAUNCH();
-    }
-    exclusive_scan_i64(ctx, c.inv_off.as<long long>(), n + 1, c.scan_tmp.p);
-    if (R > 0) {
-        k_fill_cp_inv<<<grid_for(ctx, R), 256, 0, s>>>(c.node.as<int32_t>(), R, c.inv_off.as<long long>(),
-                                                      c.fill.as<unsigned int>(), c.inv_rec.as<long long>());
-        k_init_cp<<<grid_for(ctx, R), 256, 0, s>>>(c.size.as<int32_t>(), R, c.contrib.as<int32_t>(),
-                                                  c.covered.as<uint8_t>());
-        IM_CHECK_LAUNCH();
-    }
-    greedy_scratch(ctx, gb, n, k);
-    IM_CUDA(cudaMemcpyAsync(gb.gain.p, credit, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    const int ugrid = ctx->num_sms * 8;
-    greedy_rounds(ctx, gb, n, k, [&]() {
-        k_cp_update<<<ugrid, 256, 0, s>>>(gb.state.as<GState>(), c.inv_off.as<long long>(),
-                                          c.inv_rec.as<long long>(), c.node.as<int32_t>(),
-                                          c.par.as<int32_t>(), c.size.as<int32_t>(),
-                                          c.contrib.as<int32_t>(), c.covered.as<uint8_t>(),
-                                          gb.gain.as<unsigned long long>());
-        IM_CHECK_LAUNCH();
-    });
-}
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-void greedy_lrr(imin_ctx *ctx, GreedyBufs &gb, LrrStore &L, int32_t n, int32_t k,
-                const unsigned long long *credit)
+double greedy_batch(imin_ctx *ctx, GreedyBufs &gb, std::vector<GreedyJob *> &jobs)
 {
     cudaStream_t s = ctx->stream;
-    const long long E = (long long)L.elems;
-    const uint32_t ns = L.nsets;
-    L.inv_off.ensure(ctx, (size_t)(n + 1) * 8);
-    L.inv_set.ensure(ctx, (size_t)std::max<long long>(E, 1) * 4);
-    L.fill.ensure(ctx, (size_t)(n + 1) * 4);
-    L.covered.ensure(ctx, (size_t)std::max<uint32_t>(ns, 1));
-    L.scan_tmp.ensure(ctx, scan_tmp_bytes(n + 1));
-    IM_CUDA(cudaMemsetAsync(L.inv_off.p, 0, (size_t)(n + 1) * 8, s));
-    IM_CUDA(cudaMemsetAsync(L.fill.p, 0, (size_t)(n + 1) * 4, s));
-    IM_CUDA(cudaMemsetAsync(L.covered.p, 0, (size_t)std::max<uint32_t>(ns, 1), s));
-    if (E > 0) {
-        k_count_nodes<<<grid_for(ctx, E), 256, 0, s>>>(L.elem.as<int32_t>(), E, L.inv_off.as<long long>());
-        IM_CHECK_LAUNCH();
+    const int nj = (int)jobs.size();
+    if (nj == 0) return 0.0;
+    for (GreedyJob *j : jobs) prepare_index(ctx, *j);
+    // per-instance state in one arena
+    std::vector<GInst> gi(nj);
+    std::vector<size_t> off(nj);
+    std::vector<int32_t> blk2inst, ublk2inst;
+    size_t total = 0;
+    int32_t kmax = 0;
+    for (int i = 0; i < nj; ++i) {
+        const GreedyJob &j = *jobs[i];
+        const int32_t n = j.n, k = j.k;
+        kmax = std::max(kmax, k);
+        const int nblk = (int)std::min<long long>((long long)ctx->num_sms * 4,
+                                                   std::max<long long>(1, ((long long)n + 2047) / 2048));
+        const int unblk = (int)std::min<long long>((long long)ctx->num_sms * 8,
+                                                    std::max<long long>(1, ((long long)n + 999) / 1000));
+        GInst &I = gi[i];
+        I.n = n;
+        I.k = k;
+        I.blk0 = (int32_t)blk2inst.size();
+        I.nblk = nblk;
+        for (int b = 0; b < nblk; ++b) blk2inst.push_back(i);
+        I.ublk0 = (int32_t)ublk2inst.size();
+        I.unblk = unblk;
+        for (int b = 0; b < unblk; ++b) ublk2inst.push_back(i);
+        off[i] = total;
+        total += al256((size_t)n * 8) + al256(sizeof(GState)) + al256((size_t)(k + 1) * 4) +
+                 2 * al256((size_t)(k + 2) * 8) + al256(RS_BINS * 4) + al256(RS_BINS * 8) +
+                 al256((size_t)nblk * 8) + al256((size_t)nblk * 4) + 256;
     }
-    exclusive_scan_i64(ctx, L.inv_off.as<long long>(), n + 1, L.scan_tmp.p);
-    if (ns > 0) {
-        k_fill_lrr_inv<<<grid_for(ctx, (long long)ns * 32), 256, 0, s>>>(
-            L.off.as<unsigned long long>(), L.len.as<uint32_t>(), ns, L.elem.as<int32_t>(),
-            L.inv_off.as<long long>(), L.fill.as<unsigned int>(), L.inv_set.as<uint32_t>());
-        IM_CHECK_LAUNCH();
+    gb.arena.ensure(ctx, total);
+    IM_CUDA(cudaMemsetAsync(gb.arena.p, 0, total, s));
+    char *base = reinterpret_cast<char *>(gb.arena.p);
+    for (int i = 0; i < nj; ++i) {
+        const GreedyJob &j = *jobs[i];
+        GInst &I = gi[i];
+        char *p = base + off[i];
+        auto take = [&](size_t bytes) {
+            char *q = p;
+            p += al256(bytes);
+            return q;
+        };
+        I.gain = reinterpret_cast<unsigned long long *>(take((size_t)j.n * 8));
+        I.st = reinterpret_cast<GState *>(take(sizeof(GState)));
+        I.B = reinterpret_cast<int32_t *>(take((size_t)(j.k + 1) * 4));
+        I.cov = reinterpret_cast<unsigned long long *>(take((size_t)(j.k + 2) * 8));
+        I.topk = reinterpret_cast<unsigned long long *>(take((size_t)(j.k + 2) * 8));
+        I.hcnt = reinterpret_cast<unsigned int *>(take(RS_BINS * 4));
+        I.hsum = reinterpret_cast<unsigned long long *>(take(RS_BINS * 8));
+        I.part_g = reinterpret_cast<unsigned long long *>(take((size_t)I.nblk * 8));
+        I.part_v = reinterpret_cast<int32_t *>(take((size_t)I.nblk * 4));
+        I.done_ctr = reinterpret_cast<unsigned int *>(take(4));
+        IM_CUDA(cudaMemcpyAsync(I.gain, j.credit, (size_t)j.n * 8, cudaMemcpyDeviceToDevice, s));
+        I.inv_rec = nullptr;
+        I.rnode = I.rpar = I.rsize = nullptr;
+        I.contrib = nullptr;
+        I.covered = nullptr;
+        I.inv_set = nullptr;
+        I.set_off = nullptr;
+        I.set_len = nullptr;
+        I.set_elem = nullptr;
+        if (j.c) {
+            I.inv_off = j.c->inv_off.as<long long>();
+            I.inv_rec = j.c->inv_rec.as<long long>();
+            I.rnode = j.c->node.as<int32_t>();
+            I.rpar = j.c->par.as<int32_t>();
+            I.rsize = j.c->size.as<int32_t>();
+            I.contrib = j.c->contrib.as<int32_t>();
+            I.covered = j.c->covered.as<uint8_t>();
+        } else {
+            I.inv_off = j.L->inv_off.as<long long>();
+            I.inv_set = j.L->inv_set.as<uint32_t>();
+            I.set_off = j.L->off.as<unsigned long long>();
+            I.set_len = j.L->len.as<uint32_t>();
+            I.set_elem = j.L->elem.as<int32_t>();
+            I.covered = j.L->covered.as<uint8_t>();
+        }
     }
-    greedy_scratch(ctx, gb, n, k);
-    IM_CUDA(cudaMemcpyAsync(gb.gain.p, credit, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
-    const int ugrid = ctx->num_sms * 8;
-    greedy_rounds(ctx, gb, n, k, [&]() {
-        k_lrr_update<<<ugrid, 256, 0, s>>>(gb.state.as<GState>(), L.inv_off.as<long long>(),
-                                           L.inv_set.as<uint32_t>(), L.off.as<unsigned long long>(),
-                                           L.len.as<uint32_t>(), L.elem.as<int32_t>(),
-                                           L.covered.as<uint8_t>(), gb.gain.as<unsigned long long>());
+    gb.ginst.ensure(ctx, (size_t)nj * sizeof(GInst));
+    gb.blkmap.ensure(ctx, (blk2inst.size() + ublk2inst.size()) * 4);
+    IM_CUDA(cudaMemcpyAsync(gb.ginst.p, gi.data(), (size_t)nj * sizeof(GInst), cudaMemcpyHostToDevice, s));
+    IM_CUDA(cudaMemcpyAsync(gb.blkmap.p, blk2inst.data(), blk2inst.size() * 4, cudaMemcpyHostToDevice, s));
+    IM_CUDA(cudaMemcpyAsync(gb.blkmap.as<int32_t>() + blk2inst.size(), ublk2inst.data(),
+                            ublk2inst.size() * 4, cudaMemcpyHostToDevice, s));
+    const GInst *dgi = gb.ginst.as<GInst>();
+    const int32_t *dblk = gb.blkmap.as<int32_t>();
+    const int32_t *dublk = dblk + blk2inst.size();
+    const int nb = (int)blk2inst.size(), nub = (int)ublk2inst.size();
+    // every job is either CP or LRR; both kinds may not share a batch
+    const int lrr = jobs[0]->L ? 1 : 0;
+    cudaEvent_t e0, e1;
+    IM_CUDA(cudaEventCreate(&e0));
+    IM_CUDA(cudaEventCreate(&e1));
+    IM_CUDA(cudaEventRecord(e0, s));
+    for (int32_t round = 0; round <= kmax; ++round) {
+        k_argmax<<<nb, 256, 0, s>>>(dgi, dblk, round);
         IM_CHECK_LAUNCH();
-    });
+        for (int pass = 0; pass < 6; ++pass) {
+            k_topk_hist<<<nb, 256, 0, s>>>(dgi, dblk, round);
+            IM_CHECK_LAUNCH();
+            k_topk_select<<<nj, 1024, 0, s>>>(dgi, round);
+            IM_CHECK_LAUNCH();
+        }
+        if (round < kmax) {
+            k_update<<<nub, 256, 0, s>>>(dgi, dublk, round, lrr);
+            IM_CHECK_LAUNCH();
+        }
+    }
+    IM_CUDA(cudaEventRecord(e1, s));
+    IM_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    IM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // read back B, Cov(B_i), top-k sums
+    for (int i = 0; i < nj; ++i) {
+        GreedyJob &j = *jobs[i];
+        const GInst &I = gi[i];
+        GState st;
+        IM_CUDA(cudaMemcpy(&st, I.st, sizeof(GState), cudaMemcpyDeviceToHost));
+        GreedyOut &o = j.out;
+        const int nbk = st.nb;
+        o.B.resize(nbk);
+        o.cov.resize(nbk + 1);
+        o.topk.resize(nbk + 1);
+        if (nbk > 0) IM_CUDA(cudaMemcpy(o.B.data(), I.B, (size_t)nbk * 4, cudaMemcpyDeviceToHost));
+        IM_CUDA(cudaMemcpy(o.cov.data(), I.cov, (size_t)(nbk + 1) * 8, cudaMemcpyDeviceToHost));
+        IM_CUDA(cudaMemcpy(o.topk.data(), I.topk, (size_t)(nbk + 1) * 8, cudaMemcpyDeviceToHost));
+        o.covu = o.cov[0] + o.topk[0];
+        for (int t = 1; t <= nbk; ++t) o.covu = std::min(o.covu, o.cov[t] + o.topk[t]);
+    }
+    return ms;
 }
 
 unsigned long long cov_cp(imin_ctx *ctx, CpStore &c, const uint32_t *inB, unsigned long long *d_out,

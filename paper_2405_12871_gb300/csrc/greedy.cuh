@@ -18,8 +18,54 @@ struct GState {
     int32_t pad;
 };
 
+struct CpStore;
+struct LrrStore;
+
+// One Max-Coverage instance as the batched round kernels see it.
+struct GInst {
+    int32_t n, k;
+    unsigned long long *gain;
+    GState *st;
+    int32_t *B;
+    unsigned long long *cov, *topk;
+    unsigned int *hcnt;
+    unsigned long long *hsum;
+    unsigned long long *part_g;
+    int32_t *part_v;
+    unsigned int *done_ctr;
+    int32_t blk0, nblk;      // blocks of the argmax / histogram grids
+    int32_t ublk0, unblk;    // blocks of the decrement grid
+    const long long *inv_off;
+    // CP records
+    const long long *inv_rec;
+    const int32_t *rnode, *rpar, *rsize;
+    int32_t *contrib;
+    uint8_t *covered;
+    // LRR sets
+    const uint32_t *inv_set;
+    const unsigned long long *set_off;
+    const uint32_t *set_len;
+    const int32_t *set_elem;
+};
+
+// Result of one Max-Coverage run: B_i, Cov(B_i), top-k marginal sums, Cov^u.
+struct GreedyOut {
+    std::vector<int32_t> B;
+    std::vector<unsigned long long> cov, topk;
+    unsigned long long covu = 0;
+};
+
+// A Max-Coverage job: CP records (c) or LRR sets (L), gains initialised from credit.
+struct GreedyJob {
+    CpStore *c = nullptr;
+    LrrStore *L = nullptr;
+    int32_t n = 0, k = 0;
+    const unsigned long long *credit = nullptr;
+    GreedyOut out;
+};
+
 struct GreedyBufs {
-    DBuf state, part_g, part_v, done, hcnt, hsum, B, cov, topk, gain;
+    DBuf arena, ginst, blkmap;
 };
 
 // CP records of one collection (C1 or C2), in DT preorder per world.
@@ -30,6 +76,14 @@ struct CpStore {
     unsigned long long cap = 0;
     uint64_t worlds = 0;           // |C|
     DBuf inv_off, inv_rec, fill, contrib, covered, scan_tmp;
+    void release()
+    {
+        for (DBuf *b : {&node, &par, &size, &cursor, &inv_off, &inv_rec, &fill, &contrib, &covered, &scan_tmp})
+            b->release();
+        count = 0;
+        cap = 0;
+        worlds = 0;
+    }
 };
 
 // LRR sets of one collection (L1 or L2), one slot per world (empty sets have len 0).
@@ -42,13 +96,20 @@ struct LrrStore {
     uint32_t nsets = 0;            // worlds (|L|, empty sets included)
     uint64_t worlds_cap = 0;
     DBuf inv_off, inv_set, fill, covered, scan_tmp;
+    void release()
+    {
+        for (DBuf *b : {&elem, &off, &len, &cursor, &inv_off, &inv_set, &fill, &covered, &scan_tmp})
+            b->release();
+        elems = 0;
+        cap = 0;
+        nsets = 0;
+        worlds_cap = 0;
+    }
 };
 
-void greedy_scratch(imin_ctx *ctx, GreedyBufs &gb, int32_t n, int32_t k);
-void greedy_cp(imin_ctx *ctx, GreedyBufs &gb, CpStore &c, int32_t n, int32_t k,
-               const unsigned long long *credit);
-void greedy_lrr(imin_ctx *ctx, GreedyBufs &gb, LrrStore &L, int32_t n, int32_t k,
-                const unsigned long long *credit);
+// Run every job's Max-Coverage together: one launch per round step for all jobs.
+// Returns the device time of the round kernels (CUDA events).
+double greedy_batch(imin_ctx *ctx, GreedyBufs &gb, std::vector<GreedyJob *> &jobs);
 unsigned long long cov_cp(imin_ctx *ctx, CpStore &c, const uint32_t *inB, unsigned long long *d_out,
                           unsigned long long *h_out);
 unsigned long long cov_lrr(imin_ctx *ctx, LrrStore &L, const uint32_t *inB,

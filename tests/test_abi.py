@@ -46,6 +46,8 @@ int main(void) {
   printf("imin_sample_out size %zu\n", sizeof(imin_sample_out));
   printf("imin_solve_opts size %zu\n", sizeof(imin_solve_opts));
   printf("imin_result size %zu\n", sizeof(imin_result));
+  printf("imin_query size %zu\n", sizeof(imin_query));
+  F(imin_query, opts); F(imin_query, delta);
   F(imin_sample_opts, first_sample); F(imin_sample_opts, mode);
   F(imin_sample_out, world_spread); F(imin_sample_out, nonempty_lrr);
   F(imin_solve_opts, fixed_theta); F(imin_solve_opts, variant);
@@ -64,7 +66,8 @@ def test_struct_layouts_match_header(tmp_path):
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
     lines = subprocess.check_output([str(exe)], text=True).split("\n")
     m = {"imin_sample_opts": _lib.SampleOpts, "imin_sample_out": _lib.SampleOut,
-         "imin_solve_opts": _lib.SolveOpts, "imin_result": _lib.Result}
+         "imin_solve_opts": _lib.SolveOpts, "imin_result": _lib.Result,
+         "imin_query": _lib.Query}
     n = 0
     for line in lines:
         if not line.strip():
@@ -75,7 +78,7 @@ def test_struct_layouts_match_header(tmp_path):
         else:
             assert getattr(m[t], f).offset == int(v), (t, f)
         n += 1
-    assert n == 19
+    assert n == 22
 
 
 def test_no_gpu_reports_device_error():
