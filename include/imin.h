@@ -50,7 +50,8 @@ enum imin_status {
                            or a per-world structure larger than the library supports */
     IMIN_ENOMEM = 3,    /* device memory budget exceeded, or an allocation failed */
     IMIN_EDEVICE = 4,   /* CUDA error (message available through imin_last_error) */
-    IMIN_ETIMEOUT = 5   /* a bounded device-side wait expired */
+    IMIN_ETIMEOUT = 5,  /* a bounded device-side wait expired */
+    IMIN_EAGAIN = 6     /* imin_server_poll: the query has not finished yet */
 };
 
 /* Sampling mode bits for imin_sample_opts.mode. */
@@ -221,6 +222,41 @@ typedef struct imin_query {
  * whole batch.  Errors: as imin_solve; on error no result is complete. */
 int imin_solve_batch(imin_ctx *ctx, int32_t n_inst, const imin_query *queries,
                      imin_result *results);
+
+/* ---------------------------------------------------------------------------
+ * Server: continuous batching over graphs resident in one context.  A worker
+ * thread owns the context while the server runs (the caller must not use the
+ * context from another thread meanwhile).  Submitted queries wait until the
+ * concurrency limit and the device-memory estimate admit them; admitted queries
+ * join the running scheduler between steps, so their sampling shares launches
+ * with the queries already in flight.  Each result is the same as imin_solve
+ * returns for that query alone; ms_stage[7] is its latency from submit to done.
+ */
+typedef struct imin_server imin_server;
+
+typedef struct imin_server_opts {
+    int32_t max_active;     /* queries in flight at once (<= 0: 64) */
+    int32_t reserved;
+    uint64_t mem_budget;    /* device bytes admitted queries may use (0: half the free memory) */
+} imin_server_opts;
+
+/* Start a server on ctx.  Errors: IMIN_EINVAL, IMIN_ENOMEM, IMIN_EDEVICE. */
+int imin_server_start(imin_ctx *ctx, const imin_server_opts *opts, imin_server **out);
+
+/* Queue a query (its arrays are copied); *ticket identifies it.
+ * Errors: IMIN_EINVAL (bad query, graph of another context, server stopping). */
+int imin_server_submit(imin_server *srv, const imin_query *q, uint64_t *ticket);
+
+/* Collect a query's result.  wait_ms: 0 = do not wait, > 0 = wait up to that long,
+ * < 0 = wait until done.  Returns IMIN_EAGAIN while the query runs, IMIN_OK with the
+ * result copied into res (blocker arrays caller-allocated with room for k), or the
+ * query's error; a ticket can be collected once.  latency_ms (may be NULL) receives
+ * the time from submit to completion. */
+int imin_server_poll(imin_server *srv, uint64_t ticket, int32_t wait_ms, imin_result *res,
+                     double *latency_ms);
+
+/* Finish every submitted query, stop the worker and free the server. */
+int imin_server_stop(imin_server *srv);
 
 /* Static description of a status code. */
 const char *imin_strerror(int status);

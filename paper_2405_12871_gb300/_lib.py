@@ -13,14 +13,15 @@ import numpy as np
 
 from . import build as _build
 
-IMIN_OK, IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM, IMIN_EDEVICE, IMIN_ETIMEOUT = range(6)
+IMIN_OK, IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM, IMIN_EDEVICE, IMIN_ETIMEOUT, IMIN_EAGAIN = range(7)
 IMIN_REACH, IMIN_CREDIT_LOWER, IMIN_CREDIT_UPPER, IMIN_OUT_DEVICE = 1, 2, 4, 0x100
 VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 
 # names the library must export (checked by the CPU tests against include/imin.h)
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
            "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc",
-           "imin_solve_batch"]
+           "imin_solve_batch", "imin_server_start", "imin_server_submit", "imin_server_poll",
+           "imin_server_stop"]
 NOALLOC_MAX_NODES = 2_000_000
 
 
@@ -65,6 +66,10 @@ class Query(C.Structure):
     _fields_ = [("g", C.c_void_p), ("S", C.POINTER(C.c_int32)), ("nS", C.c_int32),
                 ("k", C.c_int32), ("eps", C.c_double), ("delta", C.c_double),
                 ("opts", SolveOpts)]
+
+
+class ServerOpts(C.Structure):
+    _fields_ = [("max_active", C.c_int32), ("reserved", C.c_int32), ("mem_budget", C.c_uint64)]
 
 
 _lib = None
@@ -112,6 +117,14 @@ def load(build_if_missing: bool = True):
     L.imin_sample_reach_noalloc.restype = C.c_int
     L.imin_solve_batch.argtypes = [C.c_void_p, C.c_int32, P(Query), P(Result)]
     L.imin_solve_batch.restype = C.c_int
+    L.imin_server_start.argtypes = [C.c_void_p, P(ServerOpts), P(C.c_void_p)]
+    L.imin_server_start.restype = C.c_int
+    L.imin_server_submit.argtypes = [C.c_void_p, P(Query), P(C.c_uint64)]
+    L.imin_server_submit.restype = C.c_int
+    L.imin_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.c_int32, P(Result), P(C.c_double)]
+    L.imin_server_poll.restype = C.c_int
+    L.imin_server_stop.argtypes = [C.c_void_p]
+    L.imin_server_stop.restype = C.c_int
     _lib = L
     return L
 
@@ -337,3 +350,57 @@ def imin_sample_reach_noalloc(d_row_ptr, d_col, d_prob, n, m, S, theta, key=0, t
     if rc != IMIN_OK:
         raise IminError(rc, "imin_sample_reach_noalloc: " + L.imin_strerror(rc).decode())
     return int(tot[0]), int(tot[1])
+
+
+class Server:
+    """Continuous-batching server over graphs of one Context (imin_server_*)."""
+
+    def __init__(self, ctx: "Context", max_active: int = 64, mem_budget: int = 0):
+        L = load()
+        self.ctx = ctx
+        self.h = C.c_void_p()
+        o = ServerOpts(int(max_active), 0, int(mem_budget))
+        rc = L.imin_server_start(ctx.h, C.byref(o), C.byref(self.h))
+        _check(ctx.h, rc, "imin_server_start")
+        self.k = {}
+
+    def submit(self, G, S, k, eps, delta, **kw) -> int:
+        L = load()
+        S = _as_i32(S)
+        q = Query()
+        q.g = G.h.value if isinstance(G.h, C.c_void_p) else G.h
+        q.S = _i32p(S)
+        q.nS = len(S)
+        q.k = int(k)
+        q.eps = float(eps)
+        q.delta = float(delta)
+        q.opts = SolveOpts(float(kw.get("beta", 0.1)), float(kw.get("gamma", 0.1)),
+                           int(kw.get("key", 0)), int(kw.get("inst", 0)),
+                           VARIANTS[kw.get("variant", "sandimin")], int(kw.get("fixed_theta", 0)))
+        t = C.c_uint64()
+        rc = L.imin_server_submit(self.h, C.byref(q), C.byref(t))
+        _check(self.ctx.h, rc, "imin_server_submit")
+        self.k[int(t.value)] = int(k)
+        return int(t.value)
+
+    def poll(self, ticket: int, wait_ms: int = -1):
+        """Result dict (with 'latency_ms') when done, None while running."""
+        L = load()
+        k = self.k[ticket]
+        arrs = [np.zeros(max(k, 1), np.int32) for _ in range(4)]
+        r = Result()
+        r.blockers, r.B_L, r.B_U, r.B_R = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
+        lat = C.c_double()
+        rc = L.imin_server_poll(self.h, int(ticket), int(wait_ms), C.byref(r), C.byref(lat))
+        if rc == IMIN_EAGAIN:
+            return None
+        del self.k[ticket]
+        _check(self.ctx.h, rc, "imin_server_poll")
+        d = _result_dict(r, arrs)
+        d["latency_ms"] = float(lat.value)
+        return d
+
+    def stop(self):
+        if self.h:
+            load().imin_server_stop(self.h)
+            self.h = None

@@ -26,8 +26,13 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
+#include <deque>
 #include <functional>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <numeric>
 
 void build_device_graph(imin_graph *g, const float *h_prob);
@@ -80,6 +85,13 @@ struct Query {
     DBuf dS, dseed_bm, dblk_bm, dB, dVs;
     std::vector<int32_t> Vs;      // sorted ascending
     size_t words = 0;
+    void release()
+    {
+        for (DBuf *b : {&dS, &dseed_bm, &dblk_bm, &dB, &dVs}) b->release();
+        std::vector<int32_t>().swap(Vs);
+        std::vector<uint8_t>().swap(is_seed);
+        std::vector<uint8_t>().swap(is_blocked);
+    }
 };
 
 void check_nodes(const imin_graph *g, const int32_t *a, int32_t cnt, const char *what,
@@ -748,6 +760,8 @@ struct Inst {
     CpStore C1, C2;
     LrrStore L1, L2;
     DBuf credC1, credL1, inB;
+    int stage = 0;            // Stage of the scheduler
+    Query qb[3];              // final-estimate queries (S with B_L / B_U / B_R blocked)
 };
 
 void put(int32_t *dst, const std::vector<int32_t> &src)
@@ -879,236 +893,304 @@ bool bound_check(Inst &I, Bound &B, bool upper, uint64_t n1, uint64_t n2)
     return B.sL / B.sU >= one_m_inv_e_m_eps || B.it == B.imax;
 }
 
-struct Stage {
+// ---------------------------------------------------------------------------
+// Scheduler: advances any number of solves (Algorithm 1), each at its own stage.
+// Every step runs, for all instances at once: one stop-rule launch (spread
+// estimates and final estimates), one lower-bound sampling launch with its batched
+// Max-Coverage, and one upper-bound sampling launch with its batched Max-Coverage.
+// Instances may be added between steps (continuous batching); a result depends on
+// its own query only, because worlds are addressed by index.
+// ---------------------------------------------------------------------------
+enum Stage { ST_IHAT, ST_LSAMPLE, ST_UGATE, ST_USAMPLE, ST_FINAL, ST_DONE };
+
+struct Scheduler {
+    imin_ctx *ctx;
+    GreedyBufs gb;
+    DBuf d_cov;
+    unsigned long long h_cov = 0;
+    std::vector<Inst *> active;
     double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double kms[4] = {0, 0, 0, 0};
+    uint64_t reach_launches = 0;
+
+    explicit Scheduler(imin_ctx *c) : ctx(c) { d_cov.ensure(ctx, 16); }
+
+    void add(Inst *I)
+    {
+        if (I->done) return;
+        I->stage = ST_IHAT;
+        active.push_back(I);
+    }
+
+    // move an instance to the next bound (or the final estimates) after `from`
+    void next_after(Inst &I, int finished)   // finished: -1 none (after I_hat), 0 lower, 1 upper
+    {
+        if (finished < 0 && I.do_L) {
+            start_bound(I, false);
+            return;
+        }
+        if (finished < 1 && I.do_U) {
+            start_bound(I, true);
+            return;
+        }
+        start_final(I);
+    }
+
+    void start_bound(Inst &I, bool upper)
+    {
+        bound_init(I, upper ? I.U : I.L, upper);
+        DBuf &cred = upper ? I.credL1 : I.credC1;
+        const int32_t n = I.g->n;
+        cred.ensure(ctx, (size_t)n * 8);
+        IM_CUDA(cudaMemsetAsync(cred.p, 0, (size_t)n * 8, ctx->stream));
+        I.stage = upper ? ST_USAMPLE : ST_LSAMPLE;
+    }
+
+    void start_final(Inst &I)
+    {
+        I.res->nBR = I.k;
+        put(I.B_R, I.BRv);
+        const std::vector<int32_t> *cand[3] = {&I.BLv, &I.BUv, &I.BRv};
+        const bool use[3] = {I.do_L, I.do_U, I.do_R};
+        for (int c = 0; c < 3; ++c) {
+            I.res->I_after[c] = 0.0;
+            if (!use[c]) continue;
+            prepare_query(ctx, I.g, I.qb[c], I.q.S.data(), (int32_t)I.q.S.size(), cand[c]->data(),
+                          (int32_t)cand[c]->size(), true);
+        }
+        I.stage = ST_FINAL;
+    }
+
+    void finish(Inst &I)
+    {
+        imin_result *res = I.res;
+        const std::vector<int32_t> *cand[3] = {&I.BLv, &I.BUv, &I.BRv};
+        const bool use[3] = {I.do_L, I.do_U, I.do_R};
+        int best = -1;
+        for (int c = 0; c < 3; ++c)
+            if (use[c] && (best < 0 || res->I_after[c] < res->I_after[best])) best = c;
+        res->chosen = best;
+        res->n_blockers = (int32_t)cand[best]->size();
+        put(I.blockers, *cand[best]);
+        if (I.do_U && I.variant == IMIN_SANDIMIN && res->DU_hat > 0.0) {
+            const double one_m_inv_e_m_eps = 1.0 - 1.0 / IM_E - I.eps;
+            const double gr = (1.0 - I.gamma) * (1.0 - I.gamma) / ((1.0 + I.gamma) * (1.0 + I.gamma));
+            res->ratio_lb = gr * one_m_inv_e_m_eps * (I.I_hat - res->I_after[1]) / res->DU_hat;
+        }
+        for (int c = 0; c < 3; ++c) I.qb[c].release();
+        I.stage = ST_DONE;
+        I.done = true;
+    }
+
+    void bound_done(Inst &I, bool upper)
+    {
+        Bound &B = upper ? I.U : I.L;
+        imin_result *res = I.res;
+        res->worlds_sampled += B.st.worlds;
+        res->edges_scanned += B.st.edges;
+        if (!upper) {
+            I.BLv = B.go.B;
+            res->nBL = (int32_t)I.BLv.size();
+            put(I.B_L, I.BLv);
+            res->sigmaL_L = B.sL;
+            res->sigmaU_L = B.sU;
+            res->iters_L = B.it;
+            res->theta_C1 = I.C1.worlds;
+            res->theta_C2 = I.C2.worlds;
+            res->covC2 = B.cov2;
+            res->DL_hat = (double)B.cov2 / (double)I.C2.worlds;
+            res->theta_max_L = B.th_max;
+            I.C1.release();
+            I.C2.release();
+            I.credC1.release();
+        } else {
+            I.BUv = B.go.B;
+            res->nBU = (int32_t)I.BUv.size();
+            put(I.B_U, I.BUv);
+            res->sigmaL_U = B.sL;
+            res->sigmaU_U = B.sU;
+            res->iters_U = B.it;
+            res->theta_L1 = I.L1.nsets;
+            res->theta_L2 = I.L2.nsets;
+            res->covL2 = B.cov2;
+            res->DU_hat = (double)I.nVs * (double)B.cov2 / (double)I.L2.nsets;
+            res->theta_max_U = B.th_max;
+            I.L1.release();
+            I.L2.release();
+            I.credL1.release();
+        }
+        next_after(I, upper ? 1 : 0);
+    }
+
+    // spread estimates (Algorithm 4, line 4) and final estimates (Algorithm 1, line 4)
+    void phase_stop()
+    {
+        Timer t;
+        std::vector<StopSpec> sp;
+        std::vector<std::pair<Inst *, int>> ref;   // candidate index, -1 = spread estimate
+        for (Inst *I : active) {
+            if (I->stage == ST_IHAT) {
+                sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
+                ref.emplace_back(I, -1);
+            } else if (I->stage == ST_FINAL) {
+                const bool use[3] = {I->do_L, I->do_U, I->do_R};
+                for (int c = 0; c < 3; ++c)
+                    if (use[c]) {
+                        sp.push_back(StopSpec{I->g, &I->qb[c], I->gamma, I->delta, I->key,
+                                              (uint32_t)(5 + c), I->inst, SpreadEst{}});
+                        ref.emplace_back(I, c);
+                    }
+            }
+        }
+        if (sp.empty()) return;
+        stop_rules(ctx, sp);
+        kms[0] += sp[0].est.kernel_ms;
+        reach_launches += sp[0].est.launches;
+        bool any_ihat = false, any_final = false;
+        for (size_t i = 0; i < sp.size(); ++i) {
+            Inst &I = *ref[i].first;
+            const int c = ref[i].second;
+            const SpreadEst &e = sp[i].est;
+            imin_result *res = I.res;
+            res->worlds_sampled += e.worlds;
+            res->edges_scanned += e.edges;
+            res->reach_nodes += e.nodes;
+            res->reach_edges += e.edges;
+            if (c < 0) {
+                I.I_hat = e.I;
+                res->I_hat = e.I;
+                res->n_spread = e.N;
+                any_ihat = true;
+            } else {
+                res->I_after[c] = e.I;
+                res->n_final[c] = e.N;
+                any_final = true;
+            }
+        }
+        for (size_t i = 0; i < sp.size(); ++i) {
+            Inst &I = *ref[i].first;
+            if (ref[i].second < 0)
+                next_after(I, -1);
+            else if (I.stage == ST_FINAL)
+                finish(I);
+        }
+        const double dt = t.ms();
+        if (any_ihat && !any_final) ms[0] += dt;
+        else if (any_final && !any_ihat) ms[5] += dt;
+        else { ms[0] += dt / 2; ms[5] += dt / 2; }
+    }
+
+    // one doubling round of LSBM (upper = false) or GSBM (upper = true)
+    void phase_bound(bool upper)
+    {
+        const Stage want = upper ? ST_USAMPLE : ST_LSAMPLE;
+        std::vector<Inst *> bl;
+        for (Inst *I : active)
+            if (I->stage == want) bl.push_back(I);
+        if (bl.empty()) return;
+        Timer ts;
+        double kms_before = 0.0;
+        for (Inst *I : bl) kms_before += (upper ? I->U : I->L).st.kernel_ms;
+        if (!upper) {
+            std::vector<CpJob> jobs;
+            for (Inst *I : bl) {
+                Bound &B = I->L;
+                const double per_world = std::max(I->I_hat - (double)I->q.S.size(), 1.0);
+                jobs.push_back(CpJob{I->g, &I->q, &I->C1, 1u, I->credC1.as<unsigned long long>(),
+                                     B.from, B.to, I->key, I->inst, per_world, &B.st});
+                jobs.push_back(CpJob{I->g, &I->q, &I->C2, 2u, nullptr, B.from, B.to, I->key, I->inst,
+                                     per_world, &B.st});
+            }
+            sample_cp(ctx, jobs);
+        } else {
+            std::vector<LrrJob> jobs;
+            for (Inst *I : bl) {
+                Bound &B = I->U;
+                jobs.push_back(LrrJob{I->g, &I->q, &I->L1, 3u, I->credL1.as<unsigned long long>(),
+                                      B.from, B.to, I->key, I->inst, &B.st});
+                jobs.push_back(LrrJob{I->g, &I->q, &I->L2, 4u, nullptr, B.from, B.to, I->key, I->inst,
+                                      &B.st});
+            }
+            sample_lrr(ctx, jobs);
+        }
+        double kms_after = 0.0;
+        for (Inst *I : bl) kms_after += (upper ? I->U : I->L).st.kernel_ms;
+        kms[upper ? 2 : 1] += kms_after - kms_before;
+        ms[upper ? 3 : 1] += ts.ms();
+        // Max-Coverage on C1 / L1 of every instance of this round (one batch)
+        Timer tg;
+        std::vector<GreedyJob> gj(bl.size());
+        std::vector<GreedyJob *> gjp;
+        for (size_t i = 0; i < bl.size(); ++i) {
+            Inst *I = bl[i];
+            gj[i].n = I->g->n;
+            gj[i].k = I->k;
+            if (!upper) {
+                gj[i].c = &I->C1;
+                gj[i].credit = I->credC1.as<unsigned long long>();
+            } else {
+                gj[i].L = &I->L1;
+                gj[i].credit = I->credL1.as<unsigned long long>();
+            }
+            gjp.push_back(&gj[i]);
+        }
+        kms[3] += greedy_batch(ctx, gb, gjp);
+        for (size_t i = 0; i < bl.size(); ++i) {
+            Inst &I = *bl[i];
+            Bound &B = upper ? I.U : I.L;
+            B.go = std::move(gj[i].out);
+            B.it += 1;
+            set_bitmap_host(ctx, I.inB, I.q.words, B.go.B);
+            bool stop;
+            if (!upper) {
+                B.cov2 = cov_cp(ctx, I.C2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
+                stop = bound_check(I, B, false, I.C1.worlds, I.C2.worlds);
+            } else {
+                B.cov2 = cov_lrr(ctx, I.L2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
+                stop = bound_check(I, B, true, I.L1.nsets, I.L2.nsets);
+            }
+            if (stop) {
+                bound_done(I, upper);
+            } else {
+                // double both collections: worlds [th, 2 th)
+                B.from = B.th;
+                B.to = 2 * B.th;
+                B.th *= 2;
+            }
+        }
+        ms[upper ? 4 : 2] += tg.ms();
+    }
+
+    // one step; returns the instances finished in it
+    std::vector<Inst *> step()
+    {
+        phase_stop();
+        phase_bound(false);
+        phase_bound(true);
+        std::vector<Inst *> fin, keep;
+        for (Inst *I : active) (I->done ? fin : keep).push_back(I);
+        active.swap(keep);
+        return fin;
+    }
 };
 
 void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
 {
     Timer total;
     const unsigned long long launches0 = g_kernel_launches;
-    Stage stg;
-    GreedyBufs gb;
-    DBuf d_cov;
-    d_cov.ensure(ctx, 16);
-    unsigned long long h_cov = 0;
-    std::vector<Inst *> act;
-    for (Inst *I : all)
-        if (!I->done) act.push_back(I);
-
-    // ---- spread estimates (beta, delta/6): Algorithm 4, line 4 (one launch) ----
-    Timer t0;
-    {
-        std::vector<StopSpec> sp;
-        for (Inst *I : act)
-            sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
-        if (!sp.empty()) stop_rules(ctx, sp);
-        for (size_t i = 0; i < act.size(); ++i) {
-            Inst &I = *act[i];
-            const SpreadEst &e = sp[i].est;
-            I.I_hat = e.I;
-            I.res->I_hat = e.I;
-            I.res->n_spread = e.N;
-            I.res->worlds_sampled += e.worlds;
-            I.res->edges_scanned += e.edges;
-            I.res->reach_nodes += e.nodes;
-            I.res->reach_edges += e.edges;
-            if (i == 0) {
-                stg.kms[0] += e.kernel_ms;
-                I.res->reach_launches += e.launches;
-            }
-        }
-    }
-    stg.ms[0] = t0.ms();
-
-    // ---- LSBM (Algorithm 4) and GSBM (Sec. 5.2), all instances together ----
-    for (int upper = 0; upper < 2; ++upper) {
-        std::vector<Inst *> bl;
-        for (Inst *I : act)
-            if (upper ? I->do_U : I->do_L) {
-                bound_init(*I, upper ? I->U : I->L, upper != 0);
-                const int32_t n = I->g->n;
-                DBuf &cred = upper ? I->credL1 : I->credC1;
-                cred.ensure(ctx, (size_t)n * 8);
-                IM_CUDA(cudaMemsetAsync(cred.p, 0, (size_t)n * 8, ctx->stream));
-                bl.push_back(I);
-            }
-        double samp_ms = 0.0, greedy_ms = 0.0;
-        while (!bl.empty()) {
-            // sampling: append [from, to) to both collections of every active instance
-            Timer ts;
-            if (!upper) {
-                std::vector<CpJob> jobs;
-                for (Inst *I : bl) {
-                    Bound &B = I->L;
-                    const double per_world = std::max(I->I_hat - (double)I->q.S.size(), 1.0);
-                    jobs.push_back(CpJob{I->g, &I->q, &I->C1, 1u, I->credC1.as<unsigned long long>(),
-                                         B.from, B.to, I->key, I->inst, per_world, &B.st});
-                    jobs.push_back(CpJob{I->g, &I->q, &I->C2, 2u, nullptr, B.from, B.to, I->key,
-                                         I->inst, per_world, &B.st});
-                }
-                sample_cp(ctx, jobs);
-            } else {
-                std::vector<LrrJob> jobs;
-                for (Inst *I : bl) {
-                    Bound &B = I->U;
-                    jobs.push_back(LrrJob{I->g, &I->q, &I->L1, 3u, I->credL1.as<unsigned long long>(),
-                                          B.from, B.to, I->key, I->inst, &B.st});
-                    jobs.push_back(LrrJob{I->g, &I->q, &I->L2, 4u, nullptr, B.from, B.to, I->key,
-                                          I->inst, &B.st});
-                }
-                sample_lrr(ctx, jobs);
-            }
-            samp_ms += ts.ms();
-            // Max-Coverage on C1 / L1 of every active instance (one batch)
-            Timer tg;
-            std::vector<GreedyJob> gj(bl.size());
-            std::vector<GreedyJob *> gjp;
-            for (size_t i = 0; i < bl.size(); ++i) {
-                Inst *I = bl[i];
-                gj[i].n = I->g->n;
-                gj[i].k = I->k;
-                if (!upper) {
-                    gj[i].c = &I->C1;
-                    gj[i].credit = I->credC1.as<unsigned long long>();
-                } else {
-                    gj[i].L = &I->L1;
-                    gj[i].credit = I->credL1.as<unsigned long long>();
-                }
-                gjp.push_back(&gj[i]);
-            }
-            const double gk = greedy_batch(ctx, gb, gjp);
-            stg.kms[3] += gk;
-            std::vector<Inst *> next;
-            for (size_t i = 0; i < bl.size(); ++i) {
-                Inst &I = *bl[i];
-                Bound &B = upper ? I.U : I.L;
-                B.go = std::move(gj[i].out);
-                B.it += 1;
-                set_bitmap_host(ctx, I.inB, I.q.words, B.go.B);
-                if (!upper) {
-                    B.cov2 = cov_cp(ctx, I.C2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
-                    if (bound_check(I, B, false, I.C1.worlds, I.C2.worlds)) continue;
-                } else {
-                    B.cov2 = cov_lrr(ctx, I.L2, I.inB.as<uint32_t>(), d_cov.as<unsigned long long>(), &h_cov);
-                    if (bound_check(I, B, true, I.L1.nsets, I.L2.nsets)) continue;
-                }
-                // double both collections: worlds [th, 2 th)
-                B.from = B.th;
-                B.to = 2 * B.th;
-                B.th *= 2;
-                next.push_back(&I);
-            }
-            greedy_ms += tg.ms();
-            bl.swap(next);
-        }
-        stg.ms[upper ? 3 : 1] = samp_ms;
-        stg.ms[upper ? 4 : 2] = greedy_ms;
-        for (Inst *I : act) {
-            if (!(upper ? I->do_U : I->do_L)) continue;
-            Bound &B = upper ? I->U : I->L;
-            imin_result *res = I->res;
-            res->worlds_sampled += B.st.worlds;
-            res->edges_scanned += B.st.edges;
-            stg.kms[upper ? 2 : 1] += B.st.kernel_ms;
-            if (!upper) {
-                I->BLv = B.go.B;
-                res->nBL = (int32_t)I->BLv.size();
-                put(I->B_L, I->BLv);
-                res->sigmaL_L = B.sL;
-                res->sigmaU_L = B.sU;
-                res->iters_L = B.it;
-                res->theta_C1 = I->C1.worlds;
-                res->theta_C2 = I->C2.worlds;
-                res->covC2 = B.cov2;
-                res->DL_hat = (double)B.cov2 / (double)I->C2.worlds;
-                res->theta_max_L = B.th_max;
-            } else {
-                I->BUv = B.go.B;
-                res->nBU = (int32_t)I->BUv.size();
-                put(I->B_U, I->BUv);
-                res->sigmaL_U = B.sL;
-                res->sigmaU_U = B.sU;
-                res->iters_U = B.it;
-                res->theta_L1 = I->L1.nsets;
-                res->theta_L2 = I->L2.nsets;
-                res->covL2 = B.cov2;
-                res->DU_hat = (double)I->nVs * (double)B.cov2 / (double)I->L2.nsets;
-                res->theta_max_U = B.th_max;
-            }
-            // the collections are no longer needed
-            if (!upper) {
-                I->C1.release();
-                I->C2.release();
-            } else {
-                I->L1.release();
-                I->L2.release();
-            }
-        }
-    }
-
-    // ---- Sandwich: Algorithm 1, lines 4-5 (one launch for every candidate) ----
-    Timer tf;
-    std::vector<StopSpec> fin;
-    std::vector<std::pair<Inst *, int>> fin_ref;
-    std::vector<std::unique_ptr<Query>> qbs;
-    for (Inst *I : act) {
-        I->res->nBR = I->k;
-        put(I->B_R, I->BRv);
-        const std::vector<int32_t> *cand[3] = {&I->BLv, &I->BUv, &I->BRv};
-        const bool use[3] = {I->do_L, I->do_U, I->do_R};
-        for (int c = 0; c < 3; ++c) {
-            I->res->I_after[c] = 0.0;
-            if (!use[c]) continue;
-            qbs.emplace_back(new Query());
-            prepare_query(ctx, I->g, *qbs.back(), I->q.S.data(), (int32_t)I->q.S.size(),
-                          cand[c]->data(), (int32_t)cand[c]->size(), true);
-            fin.push_back(StopSpec{I->g, qbs.back().get(), I->gamma, I->delta, I->key,
-                                   (uint32_t)(5 + c), I->inst, SpreadEst{}});
-            fin_ref.emplace_back(I, c);
-        }
-    }
-    if (!fin.empty()) stop_rules(ctx, fin);
-    for (size_t i = 0; i < fin.size(); ++i) {
-        Inst &I = *fin_ref[i].first;
-        const int c = fin_ref[i].second;
-        const SpreadEst &e = fin[i].est;
-        imin_result *res = I.res;
-        res->I_after[c] = e.I;
-        res->n_final[c] = e.N;
-        res->worlds_sampled += e.worlds;
-        res->edges_scanned += e.edges;
-        res->reach_nodes += e.nodes;
-        res->reach_edges += e.edges;
-        if (i == 0) {
-            stg.kms[0] += e.kernel_ms;
-            res->reach_launches += e.launches;
-        }
-    }
-    stg.ms[5] = tf.ms();
-    for (Inst *I : act) {
-        imin_result *res = I->res;
-        const std::vector<int32_t> *cand[3] = {&I->BLv, &I->BUv, &I->BRv};
-        const bool use[3] = {I->do_L, I->do_U, I->do_R};
-        int best = -1;
-        for (int c = 0; c < 3; ++c)
-            if (use[c] && (best < 0 || res->I_after[c] < res->I_after[best])) best = c;
-        res->chosen = best;
-        res->n_blockers = (int32_t)cand[best]->size();
-        put(I->blockers, *cand[best]);
-        if (I->do_U && I->variant == IMIN_SANDIMIN && res->DU_hat > 0.0) {
-            const double one_m_inv_e_m_eps = 1.0 - 1.0 / IM_E - I->eps;
-            const double gr = (1.0 - I->gamma) * (1.0 - I->gamma) / ((1.0 + I->gamma) * (1.0 + I->gamma));
-            res->ratio_lb = gr * one_m_inv_e_m_eps * (I->I_hat - res->I_after[1]) / res->DU_hat;
-        }
-    }
-    stg.ms[7] = total.ms();
-    stg.ms[6] = stg.ms[7] - stg.ms[0] - stg.ms[1] - stg.ms[2] - stg.ms[3] - stg.ms[4] - stg.ms[5];
+    Scheduler sch(ctx);
+    for (Inst *I : all) sch.add(I);
+    while (!sch.active.empty()) sch.step();
+    sch.ms[7] = total.ms();
+    sch.ms[6] = sch.ms[7] - sch.ms[0] - sch.ms[1] - sch.ms[2] - sch.ms[3] - sch.ms[4] - sch.ms[5];
     // stage times and device times belong to the whole batch: every result reports them
+    bool any = false;
+    for (Inst *I : all) any |= I->stage == ST_DONE;
     for (Inst *I : all) {
-        for (int i = 0; i < 8; ++i) I->res->ms_stage[i] = I->done && act.empty() ? 0.0 : stg.ms[i];
-        for (int i = 0; i < 4; ++i) I->res->kernel_ms[i] = stg.kms[i];
+        for (int i = 0; i < 8; ++i) I->res->ms_stage[i] = any ? sch.ms[i] : 0.0;
+        if (!any) I->res->ms_stage[7] = total.ms();
+        for (int i = 0; i < 4; ++i) I->res->kernel_ms[i] = sch.kms[i];
+        I->res->reach_launches = sch.reach_launches;
         I->res->kernel_launches = g_kernel_launches - launches0;
     }
 }
@@ -1150,6 +1232,7 @@ const char *imin_strerror(int status)
     case IMIN_ENOMEM: return "out of device memory or over budget";
     case IMIN_EDEVICE: return "CUDA device error";
     case IMIN_ETIMEOUT: return "bounded device wait expired";
+    case IMIN_EAGAIN: return "not finished yet";
     default: return "unknown status";
     }
 }
@@ -1378,6 +1461,258 @@ int imin_solve_batch(imin_ctx *ctx, int32_t n_inst, const imin_query *queries, i
         }
         solve_all(ctx, all);
     });
+}
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Server: continuous batching over resident graphs.  A worker thread owns the
+// scheduler; queries are admitted between steps while the concurrency limit and the
+// device-memory estimate allow, so new queries join launches already serving others.
+// ---------------------------------------------------------------------------
+struct SrvJob {
+    uint64_t ticket = 0;
+    imin_query q;
+    std::vector<int32_t> S, blockers, BL, BU, BR;
+    imin_result res;
+    std::unique_ptr<Inst> inst;
+    int status = 0;           // 0 queued, 1 running, 2 done, 3 failed
+    int err = IMIN_OK;
+    size_t mem = 0;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+}  // namespace
+
+struct imin_server {
+    imin_ctx *ctx = nullptr;
+    int32_t max_active = 64;
+    size_t mem_budget = 0;
+    size_t mem_in_use = 0;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    bool stopping = false;
+    std::deque<SrvJob *> pending;
+    std::vector<SrvJob *> running;
+    std::map<uint64_t, std::unique_ptr<SrvJob>> jobs;
+    uint64_t next_ticket = 1;
+    uint64_t completed = 0;
+    std::string fatal;
+};
+
+namespace {
+
+// device bytes a query may need beyond its resident graph (bitmaps, credit and gain
+// arrays, V'_s, and collections of a few thousand worlds), used for admission only
+size_t query_mem_estimate(const imin_graph *g)
+{
+    return ((size_t)16 << 20) + (size_t)g->n * 96u;
+}
+
+void server_loop(imin_server *srv)
+{
+    imin_ctx *ctx = srv->ctx;
+    cudaSetDevice(ctx->device);
+    Scheduler sch(ctx);
+    for (;;) {
+        std::vector<SrvJob *> admit;
+        {
+            std::unique_lock<std::mutex> lk(srv->mu);
+            srv->cv.wait(lk, [&] { return srv->stopping || !srv->pending.empty() || !srv->running.empty(); });
+            if (srv->stopping && srv->pending.empty() && srv->running.empty()) break;
+            while (!srv->pending.empty() && (int32_t)srv->running.size() + (int32_t)admit.size() < srv->max_active) {
+                SrvJob *j = srv->pending.front();
+                if (srv->mem_in_use + j->mem > srv->mem_budget && !(srv->running.empty() && admit.empty()))
+                    break;   // wait until memory frees up (a lone query is always admitted)
+                srv->pending.pop_front();
+                srv->mem_in_use += j->mem;
+                j->status = 1;
+                admit.push_back(j);
+            }
+        }
+        // prepare the admitted queries (host work and small uploads)
+        for (SrvJob *j : admit) {
+            const int rc = run_guarded(ctx, [&] { inst_prepare(ctx, *j->inst, j->S.data(), (int32_t)j->S.size()); });
+            std::lock_guard<std::mutex> lk(srv->mu);
+            if (rc != IMIN_OK) {
+                j->status = 3;
+                j->err = rc;
+                j->t_done = std::chrono::steady_clock::now();
+                srv->mem_in_use -= j->mem;
+                srv->done_cv.notify_all();
+                continue;
+            }
+            if (j->inst->done) {   // answered by ON at once
+                j->status = 2;
+                j->t_done = std::chrono::steady_clock::now();
+                srv->mem_in_use -= j->mem;
+                srv->completed++;
+                srv->done_cv.notify_all();
+                continue;
+            }
+            sch.add(j->inst.get());
+            srv->running.push_back(j);
+        }
+        if (sch.active.empty()) continue;
+        std::vector<Inst *> fin;
+        const int rc = run_guarded(ctx, [&] { fin = sch.step(); });
+        std::lock_guard<std::mutex> lk(srv->mu);
+        const auto now = std::chrono::steady_clock::now();
+        if (rc != IMIN_OK) {
+            // a failed step fails every query it was serving
+            for (SrvJob *j : srv->running) {
+                j->status = 3;
+                j->err = rc;
+                j->t_done = now;
+                srv->mem_in_use -= j->mem;
+            }
+            srv->running.clear();
+            sch.active.clear();
+            srv->done_cv.notify_all();
+            continue;
+        }
+        std::vector<SrvJob *> still;
+        for (SrvJob *j : srv->running) {
+            if (j->inst->done) {
+                j->status = 2;
+                j->t_done = now;
+                j->res.ms_stage[7] =
+                    std::chrono::duration<double, std::milli>(now - j->t_submit).count();
+                srv->mem_in_use -= j->mem;
+                srv->completed++;
+            } else {
+                still.push_back(j);
+            }
+        }
+        srv->running.swap(still);
+        if (!fin.empty()) srv->done_cv.notify_all();
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int imin_server_start(imin_ctx *ctx, const imin_server_opts *opts, imin_server **out)
+{
+    if (!ctx || !out) return IMIN_EINVAL;
+    *out = nullptr;
+    imin_server *srv = new (std::nothrow) imin_server();
+    if (!srv) return IMIN_ENOMEM;
+    srv->ctx = ctx;
+    if (opts && opts->max_active > 0) srv->max_active = opts->max_active;
+    size_t freeb = 0, totalb = 0;
+    cudaSetDevice(ctx->device);
+    cudaMemGetInfo(&freeb, &totalb);
+    cudaGetLastError();
+    srv->mem_budget = (opts && opts->mem_budget) ? (size_t)opts->mem_budget : freeb / 2;
+    try {
+        srv->worker = std::thread(server_loop, srv);
+    } catch (...) {
+        delete srv;
+        return IMIN_EDEVICE;
+    }
+    *out = srv;
+    return IMIN_OK;
+}
+
+int imin_server_submit(imin_server *srv, const imin_query *q, uint64_t *ticket)
+{
+    if (!srv || !q || !ticket || !q->g || q->g->ctx != srv->ctx || q->nS < 1 || !q->S || q->k < 1)
+        return IMIN_EINVAL;
+    std::unique_ptr<SrvJob> j(new (std::nothrow) SrvJob());
+    if (!j) return IMIN_ENOMEM;
+    j->q = *q;
+    j->S.assign(q->S, q->S + q->nS);
+    j->blockers.resize(q->k);
+    j->BL.resize(q->k);
+    j->BU.resize(q->k);
+    j->BR.resize(q->k);
+    std::memset(&j->res, 0, sizeof(j->res));
+    j->res.blockers = j->blockers.data();
+    j->res.B_L = j->BL.data();
+    j->res.B_U = j->BU.data();
+    j->res.B_R = j->BR.data();
+    j->inst.reset(new Inst());
+    Inst &I = *j->inst;
+    I.g = q->g;
+    I.k = q->k;
+    I.eps = q->eps;
+    I.delta = q->delta;
+    I.beta = q->opts.beta;
+    I.gamma = q->opts.gamma;
+    I.key = q->opts.key;
+    I.inst = q->opts.inst;
+    I.variant = q->opts.variant;
+    I.fixed_theta = q->opts.fixed_theta;
+    I.res = &j->res;
+    I.blockers = j->res.blockers;
+    I.B_L = j->res.B_L;
+    I.B_U = j->res.B_U;
+    I.B_R = j->res.B_R;
+    j->mem = query_mem_estimate(q->g);
+    j->t_submit = std::chrono::steady_clock::now();
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stopping) return IMIN_EINVAL;
+    j->ticket = srv->next_ticket++;
+    *ticket = j->ticket;
+    srv->pending.push_back(j.get());
+    srv->jobs[j->ticket] = std::move(j);
+    srv->cv.notify_all();
+    return IMIN_OK;
+}
+
+int imin_server_poll(imin_server *srv, uint64_t ticket, int32_t wait_ms, imin_result *res,
+                     double *latency_ms)
+{
+    if (!srv || !res || !res->blockers) return IMIN_EINVAL;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return IMIN_EINVAL;
+    SrvJob *j = it->second.get();
+    auto ready = [&] { return j->status >= 2; };
+    if (!ready()) {
+        if (wait_ms > 0)
+            srv->done_cv.wait_for(lk, std::chrono::milliseconds(wait_ms), ready);
+        else if (wait_ms < 0)
+            srv->done_cv.wait(lk, ready);
+    }
+    if (!ready()) return IMIN_EAGAIN;
+    if (j->status == 3) {
+        const int e = j->err;
+        srv->jobs.erase(it);
+        return e;
+    }
+    int32_t *bl = res->blockers, *bL = res->B_L, *bU = res->B_U, *bR = res->B_R;
+    *res = j->res;
+    res->blockers = bl;
+    res->B_L = bL;
+    res->B_U = bU;
+    res->B_R = bR;
+    std::copy(j->blockers.begin(), j->blockers.begin() + j->res.n_blockers, bl);
+    if (bL) std::copy(j->BL.begin(), j->BL.begin() + j->res.nBL, bL);
+    if (bU) std::copy(j->BU.begin(), j->BU.begin() + j->res.nBU, bU);
+    if (bR) std::copy(j->BR.begin(), j->BR.begin() + j->res.nBR, bR);
+    if (latency_ms)
+        *latency_ms = std::chrono::duration<double, std::milli>(j->t_done - j->t_submit).count();
+    srv->jobs.erase(it);
+    return IMIN_OK;
+}
+
+int imin_server_stop(imin_server *srv)
+{
+    if (!srv) return IMIN_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stopping = true;
+        srv->cv.notify_all();
+    }
+    if (srv->worker.joinable()) srv->worker.join();
+    delete srv;
+    return IMIN_OK;
 }
 
 }  // extern "C"

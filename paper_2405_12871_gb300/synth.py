@@ -214,3 +214,52 @@ def workload_rmat4m(scale: int = 22):
     g = rmat(scale, 16, seed=1)
     S = seeds_uniform(g.n, 100, seed=2)
     return g, S, dict(k=200, eps=0.1, delta=1.0 / g.n, key=0)
+
+
+def chung_lu_poisson(n: int, avg_deg: float = 10.0, exponent: float = 2.1, seed: int = 1) -> Graph:
+    """Directed Chung-Lu graph in the Poisson edge model, generated in O(n + m) already
+    grouped by source: node u gets Poisson(avg_deg * n * w_out(u)) out-edges whose
+    targets are drawn with probability proportional to w_in.  Weights follow the
+    continuous power law x^(-1/(exponent-1)) on [1, n+1), under independent random
+    permutations for out- and in-weights; targets are drawn by inverting its CDF.
+    Multi-edges and self-loops are kept (each edge is an independent coin).  WC p."""
+    rng = _rng(seed)
+    a = 1.0 / (exponent - 1.0)
+    x = np.arange(1, n + 1, dtype=np.float64)
+    w = np.power(x, -a)
+    w /= w.sum()
+    perm_out = rng.permutation(n)
+    perm_in = rng.permutation(n)
+    deg = rng.poisson(avg_deg * n * w)                     # out-degree of rank r
+    deg_node = np.empty(n, np.int64)
+    deg_node[perm_out] = deg
+    row_ptr = np.zeros(n + 1, np.int64)
+    np.cumsum(deg_node, out=row_ptr[1:])
+    m = int(row_ptr[-1])
+    # inverse CDF of the continuous law on [1, n+1): rank = floor(x) - 1
+    u = rng.random(m)
+    one_m_a = 1.0 - a
+    hi = np.power(float(n + 1), one_m_a) - 1.0
+    r = np.floor(np.power(1.0 + u * hi, 1.0 / one_m_a)).astype(np.int64) - 1
+    np.clip(r, 0, n - 1, out=r)
+    col = perm_in[r].astype(np.int32)
+    g = Graph(n, row_ptr.astype(np.int32), col, np.ones(m, np.float32), f"clp-{n}")
+    return weighted_cascade(g)
+
+
+def workload_batch(count: int = 512, seed: int = 3):
+    """The batched workload: `count` independent instances on Chung-Lu graphs with
+    n log-uniform in [10^3, 10^6], average degree 10, exponent 2.1, WC p; |S| uniform
+    in [5, 100] from the top-1% out-degree nodes (pool widened to >= 2|S|); k uniform
+    in [10, 200]; eps = 0.2, delta = 1/n.  Returns a list of (graph, S, cfg)."""
+    rng = _rng(seed)
+    ns = np.round(np.power(10.0, rng.uniform(3.0, 6.0, size=count))).astype(np.int64)
+    nS = rng.integers(5, 101, size=count)
+    ks = rng.integers(10, 201, size=count)
+    out = []
+    for i in range(count):
+        g = chung_lu_poisson(int(ns[i]), 10.0, 2.1, seed=1000 + i)
+        S = seeds_top_outdeg(g, int(nS[i]), 0.01, seed=5000 + i)
+        k = int(min(ks[i], g.n - len(S) - 1))
+        out.append((g, S, dict(k=k, eps=0.2, delta=1.0 / g.n, key=0, inst=i)))
+    return out
