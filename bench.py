@@ -174,6 +174,114 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+def run_batch(args):
+    """Batched vs plain on the same instances (identical results are checked)."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    t0 = time.time()
+    items = synth.workload_batch(args.batch)
+    gen_s = time.time() - t0
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    Gs = [ctx.load_graph(g) for g, _, _ in items]
+    qs = [(G, S, c["k"], c["eps"], c["delta"], dict(key=c["key"], inst=c["inst"]))
+          for G, (g, S, c) in zip(Gs, items)]
+    # warm-up on a small instance (loads the kernels, sizes the slot arenas)
+    small = min(range(len(items)), key=lambda i: items[i][0].n)
+    G, S, k, eps, delta, kw = qs[small]
+    G.solve(S, k, eps, delta, **kw)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    plain = [G.solve(S, k, eps, delta, **kw) for (G, S, k, eps, delta, kw) in qs]
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - a
+    a = time.perf_counter()
+    batched = ctx.solve_batch(qs)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - a
+    same = all(list(x["blockers"]) == list(y["blockers"]) and x["I_after"] == y["I_after"]
+               for x, y in zip(plain, batched))
+    line = {"mode": "batch", "instances": len(items), "plain_s": t_plain, "batched_s": t_batch,
+            "speedup": t_plain / t_batch, "plain_inst_per_s": len(items) / t_plain,
+            "batched_inst_per_s": len(items) / t_batch, "identical_results": same,
+            "total_nodes": int(sum(g.n for g, _, _ in items)),
+            "total_edges": int(sum(g.m for g, _, _ in items)),
+            "batched_kernel_launches": int(batched[0]["kernel_launches"]),
+            "plain_kernel_launches": int(sum(x["kernel_launches"] for x in plain)),
+            "config": {"workload": "batch of Chung-Lu instances", "n": "log-uniform 1e3..1e6",
+                       "avg_degree": 10, "exponent": 2.1, "seeds": "U{5..100} from top-1% out-degree",
+                       "k": "U{10..200}", "eps": 0.2, "delta": "1/n"}, "graph_gen_s": gen_s}
+    print(json.dumps(line), flush=True)
+    for G in Gs:
+        G.free()
+    ctx.close()
+    return 0 if same else 1
+
+
+def run_serve(args):
+    """Poisson stream through the server; the same stream replayed one query at a time
+    (first come, first served) gives the plain latency and throughput."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    rng = np.random.Generator(np.random.Philox(77))
+    sizes = (100_000, 300_000, 1_000_000)
+    graphs = [synth.chung_lu_poisson(n, 10.0, 2.1, seed=21 + i) for i, n in enumerate(sizes)]
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    Gs = [ctx.load_graph(g) for g in graphs]
+    nq = int(rng.poisson(args.serve_rate * args.serve_seconds))
+    arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, size=nq))
+    qs = []
+    for i in range(nq):
+        gi = int(rng.integers(0, len(graphs)))
+        g = graphs[gi]
+        nS = int(rng.integers(10, 201))
+        S = np.sort(rng.choice(g.n, nS, replace=False)).astype(np.int32)
+        k = int(min(rng.integers(10, 501), g.n - nS - 1))
+        qs.append((Gs[gi], S, k, 0.2, 1.0 / g.n, dict(key=i, inst=i)))
+    # warm-up
+    G, S, k, eps, delta, kw = qs[0]
+    G.solve(S, k, eps, delta, **kw)
+    srv = _lib.Server(ctx, max_active=32)
+    t0 = time.perf_counter()
+    tickets = []
+    for (G, S, k, eps, delta, kw), at in zip(qs, arrivals):
+        now = time.perf_counter() - t0
+        if at > now:
+            time.sleep(at - now)
+        tickets.append(srv.submit(G, S, k, eps, delta, **kw))
+    served = [srv.poll(t, wait_ms=-1) for t in tickets]
+    t_served = time.perf_counter() - t0
+    srv.stop()
+    lat_s = np.array([r["latency_ms"] for r in served]) / 1e3
+    # plain replay
+    service = []
+    plain = []
+    for (G, S, k, eps, delta, kw) in qs:
+        a = time.perf_counter()
+        plain.append(G.solve(S, k, eps, delta, **kw))
+        service.append(time.perf_counter() - a)
+    free_at, lat_p = 0.0, []
+    for at, sv in zip(arrivals, service):
+        start = max(at, free_at)
+        free_at = start + sv
+        lat_p.append(free_at - at)
+    lat_p = np.array(lat_p)
+    same = all(list(x["blockers"]) == list(y["blockers"]) for x, y in zip(plain, served))
+    line = {"mode": "serve", "queries": nq, "rate_per_s": args.serve_rate,
+            "duration_s": args.serve_seconds, "served_qps": nq / t_served,
+            "served_p50_s": float(np.percentile(lat_s, 50)), "served_p99_s": float(np.percentile(lat_s, 99)),
+            "plain_qps": nq / float(np.sum(service)), "plain_p50_s": float(np.percentile(lat_p, 50)),
+            "plain_p99_s": float(np.percentile(lat_p, 99)), "identical_results": same,
+            "config": {"graphs": "Chung-Lu (Poisson model) 1e5 / 3e5 / 1e6 nodes, degree 10, WC p",
+                       "arrivals": "Poisson", "seeds": "U{10..200} uniform nodes", "k": "U{10..500}",
+                       "eps": 0.2, "delta": "1/n", "max_active": 32}}
+    print(json.dumps(line), flush=True)
+    for G in Gs:
+        G.free()
+    ctx.close()
+    return 0 if same else 1
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -182,6 +290,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="batched vs plain: the first N instances of the 512-instance Chung-Lu "
+                         "batch recipe, solved one by one and as one imin_solve_batch")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving: Poisson query stream over resident graphs through the "
+                         "continuous-batching server vs a plain one-at-a-time replay")
+    ap.add_argument("--serve-rate", type=float, default=4.0)
+    ap.add_argument("--serve-seconds", type=float, default=15.0)
     ap.add_argument("--reach-only-worlds", type=int, default=0,
                     help="profiling case: run two imin_sample launches of this many reach-only "
                          "worlds on the same workload (the stopping rule's kernel) and exit")
@@ -191,6 +307,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.batch:
+        return run_batch(args)
+    if args.serve:
+        return run_serve(args)
 
     import torch
     import torch.distributed as dist

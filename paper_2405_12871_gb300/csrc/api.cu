@@ -435,12 +435,14 @@ struct StopSpec {
 
 void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
 {
+    // Worlds are drawn in index order in chunks: each launch serves every unfinished
+    // estimate over its next range of worlds, with the threshold still missing as its
+    // early-exit bound; the host scans the sizes in order to find N exactly.
     const size_t ns = specs.size();
-    std::vector<TaskRun> tr(ns);
-    std::vector<TaskRun *> tp;
-    std::vector<DBuf> spread(ns);
     std::vector<double> W(ns), ups1(ns);
-    std::vector<unsigned long long> T(ns);
+    std::vector<unsigned long long> T(ns), sum(ns, 0);
+    std::vector<uint64_t> first(ns, 0), N(ns, 0), chunk(ns);
+    std::vector<DBuf> spread(ns);
     for (size_t i = 0; i < ns; ++i) {
         StopSpec &sp = specs[i];
         W[i] = (double)sp.q->Vs.size() + (double)sp.q->S.size();
@@ -451,44 +453,71 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
         T[i] = (unsigned long long)Td;
         // every world reaches at least |S| nodes, so N <= ceil(T / |S|)
         const uint64_t nmax = (T[i] + sp.q->S.size() - 1) / sp.q->S.size();
-        if (nmax >= ((uint64_t)1 << 31)) fail(IMIN_ERANGE, "the stopping rule may need >= 2^31 worlds");
-        spread[i].ensure(ctx, (size_t)nmax * 4 + 16);
-        tr[i].g = sp.g;
-        tr[i].q = qdev(*sp.q, sp.key, sp.tag, sp.inst);
-        tr[i].first = 0;
-        tr[i].count = (uint32_t)nmax;
-        tr[i].out.world_spread = spread[i].as<uint32_t>();
-        tr[i].out.stop_T = T[i];
-        tp.push_back(&tr[i]);
+        if (nmax >= ((uint64_t)1 << 32) - 1) fail(IMIN_ERANGE, "the stopping rule may need >= 2^32 worlds");
+        uint64_t c0 = (uint64_t)1 << 21;
+        // test hook: IMIN_STOP_CHUNK sets the first chunk (to exercise several chunks)
+        if (const char *env = std::getenv("IMIN_STOP_CHUNK")) {
+            const long long v = std::strtoll(env, nullptr, 10);
+            if (v > 0) c0 = (uint64_t)v;
+        }
+        chunk[i] = std::min<uint64_t>(nmax, c0);
     }
-    Runner run(ctx);
-    run.run(tp, WF_STOP | WF_SPREAD);
-    for (size_t i = 0; i < ns; ++i) {
-        // every claimed world is complete (deferred ones were re-run), and the worlds
-        // below the last claimed index hold at least T reached nodes in total
-        const uint64_t want = tr[i].claimed_main;
-        std::vector<uint32_t> sizes(want);
-        if (want) IM_CUDA(cudaMemcpy(sizes.data(), spread[i].p, want * 4, cudaMemcpyDeviceToHost));
-        unsigned long long sum = 0;
-        uint64_t N = 0;
-        for (uint64_t j = 0; j < want; ++j) {
-            sum += sizes[j];
-            if (sum >= T[i]) {
-                N = j + 1;
-                break;
+    double kms = 0.0;
+    uint64_t launches = 0;
+    for (;;) {
+        std::vector<TaskRun> tr(ns);
+        std::vector<TaskRun *> tp;
+        std::vector<size_t> idx;
+        for (size_t i = 0; i < ns; ++i) {
+            if (N[i]) continue;
+            const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
+            spread[i].ensure(ctx, (size_t)cnt * 4 + 16);
+            TaskRun &t = tr[i];
+            t.g = specs[i].g;
+            t.q = qdev(*specs[i].q, specs[i].key, specs[i].tag, specs[i].inst);
+            t.first = first[i];
+            t.count = (uint32_t)cnt;
+            t.out.world_spread = spread[i].as<uint32_t>();
+            t.out.stop_T = T[i] - sum[i];
+            tp.push_back(&t);
+            idx.push_back(i);
+        }
+        if (tp.empty()) break;
+        Runner run(ctx);
+        run.run(tp, WF_STOP | WF_SPREAD);
+        kms += run.kernel_ms;
+        launches += (uint64_t)run.launches;
+        for (size_t i : idx) {
+            // every claimed world is complete (deferred ones were re-run)
+            const uint64_t want = tr[i].claimed_main;
+            std::vector<uint32_t> sizes(want);
+            if (want) IM_CUDA(cudaMemcpy(sizes.data(), spread[i].p, want * 4, cudaMemcpyDeviceToHost));
+            for (uint64_t j = 0; j < want; ++j) {
+                sum[i] += sizes[j];
+                if (sum[i] >= T[i]) {
+                    N[i] = first[i] + j + 1;
+                    break;
+                }
+            }
+            SpreadEst &r = specs[i].est;
+            r.worlds += tr[i].acc[4];
+            r.edges += tr[i].acc[1];
+            r.nodes += tr[i].acc[0];
+            if (!N[i]) {
+                if (want < tr[i].count) fail(IMIN_EDEVICE, "stopping rule: threshold not reached");
+                first[i] += want;
+                chunk[i] = std::min<uint64_t>(chunk[i] * 2, (uint64_t)1 << 30);
             }
         }
-        if (N == 0) fail(IMIN_EDEVICE, "stopping rule: threshold not reached by the traversed worlds");
-        SpreadEst &r = specs[i].est;
-        r.N = N;
-        r.I = W[i] * ups1[i] / (double)N;
-        r.worlds = tr[i].acc[4];
-        r.edges = tr[i].acc[1];
-        r.nodes = tr[i].acc[0];
     }
-    // device time is shared by the tasks of the launch: report it on the first
-    specs[0].est.kernel_ms = run.kernel_ms;
-    specs[0].est.launches = (uint64_t)run.launches;
+    for (size_t i = 0; i < ns; ++i) {
+        SpreadEst &r = specs[i].est;
+        r.N = N[i];
+        r.I = W[i] * ups1[i] / (double)N[i];
+    }
+    // device time is shared by the tasks of the launches: report it on the first
+    specs[0].est.kernel_ms = kms;
+    specs[0].est.launches = launches;
 }
 
 SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double beta, double dprime,

@@ -88,3 +88,18 @@ def test_solve_validation(ctx):
             G.solve(S, **kw)
         assert e.value.code == _lib.IMIN_EINVAL
     G.free()
+
+
+def test_stopping_rule_in_many_chunks(ctx, monkeypatch):
+    """The stopping rule draws worlds in index order over several launches (small
+    first chunk); the worlds it stops at, and so every result, stay the oracle's."""
+    g, S, cfg = synth.workload_er1k()
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=5, eps=0.3, delta=1.0 / g.n, key=5, fixed_theta=500)
+    monkeypatch.setenv("IMIN_STOP_CHUNK", "997")
+    got = G.solve(S, **kw)
+    monkeypatch.delenv("IMIN_STOP_CHUNK")
+    compare(got, og.solve(S, **kw))
+    assert got["n_spread"] > 5 * 997
+    G.free()
