@@ -221,6 +221,33 @@ struct Runner {
         if (ev1) cudaEventDestroy(ev1);
     }
 
+    const SlotCfg *force = nullptr;     // autotuner: launch configuration to time
+    const imin_graph *gref = nullptr;   // graph whose tuned configuration applies
+
+    // slot memory of at most half the free device memory (and half the budget left)
+    size_t slot_avail(size_t *freeb_out = nullptr) const
+    {
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        size_t avail = freeb / 2;
+        if (ctx->budget)
+            avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
+        if (freeb_out) *freeb_out = freeb;
+        return avail;
+    }
+
+    SlotCfg cap_ctas(SlotCfg c) const
+    {
+        size_t freeb = 0;
+        const size_t avail = slot_avail(&freeb);
+        const size_t per = c.bytes_per_slot();
+        const size_t maxc = per ? avail / per : (size_t)c.ctas;
+        if ((size_t)c.ctas > maxc) c.ctas = (int)std::max<size_t>(maxc, 1);
+        if (per > freeb) fail(IMIN_ENOMEM, "not enough device memory for sampling slots");
+        c.warps = c.ctas * (c.cta_threads / 32);
+        return c;
+    }
+
     SlotCfg cfg_for(uint32_t flags, int32_t n, int64_t m, int32_t nS, bool big) const
     {
         SlotCfg c;
@@ -231,6 +258,44 @@ struct Runner {
         if (const char *env = std::getenv("IMIN_GROUPS_PER_LANE")) {
             const long v = std::strtol(env, nullptr, 10);
             if (v == 1 || v == 2 || v == 4) c.groups_per_lane = (int)v;
+        }
+        // reach-only worlds: one world per CTA, as many CTAs as fit on an SM, the visited
+        // bitmap in shared memory when n bits fit; the autotuner's choice for the graph
+        // wins when there is one (IMIN_REACH_CTA=0 selects the warp-per-world kernel)
+        const char *cta_env = std::getenv("IMIN_REACH_CTA");
+        if (!c.lower && !c.upper && !big) {
+            if (force) return cap_ctas(*force);   // autotuner probe
+            const bool env_warp = cta_env && cta_env[0] == '0';
+            if (gref && gref->tuned_ctas > 0 && !env_warp) {
+                c.smem_bm = gref->tuned_smem;
+                c.cta_threads = gref->tuned_bd;
+                c.qcap = n + 1;
+                c.ecap = 0;
+                c.ctas = gref->tuned_ctas;
+                c.warps = c.ctas * (c.cta_threads / 32);
+                return cap_ctas(c);
+            }
+            if (!env_warp && !(gref && gref->tuned_ctas < 0)) {
+                int optin = 0;
+                cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+                cudaGetLastError();
+                // test hooks: IMIN_REACH_BD picks the CTA size, IMIN_REACH_SMEM=0 keeps the
+                // visited bitmap in global memory
+                int bd = 1024;
+                if (const char *env = std::getenv("IMIN_REACH_BD")) {
+                    const long v = std::strtol(env, nullptr, 10);
+                    if (v == 256 || v == 512) bd = (int)v;
+                }
+                c.smem_bm = c.bm_words * 4 + cta_static_smem(bd) + 1024 <= (size_t)optin;
+                if (const char *env = std::getenv("IMIN_REACH_SMEM"))
+                    if (env[0] == '0') c.smem_bm = false;
+                c.cta_threads = bd;
+                c.qcap = n + 1;
+                c.ecap = 0;
+                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, c.smem_bm, c.bm_words));
+                c.warps = c.ctas * (bd / 32);
+                return cap_ctas(c);
+            }
         }
         if (big) {
             c.qcap = n + 1;
@@ -247,6 +312,7 @@ struct Runner {
             c.qcap = std::min<int32_t>(n + 1, std::max<int32_t>(q, nS + 1));
             c.ecap = c.lower ? (int32_t)std::min<int64_t>(std::max<int64_t>(m, 1), 2 * (int64_t)c.qcap) : 0;
             int per_sm = c.lower ? 8 : 32;
+            if (!c.lower && !c.upper && gref && gref->tuned_ctas < 0) per_sm = -gref->tuned_ctas;
             // tuning hook: IMIN_SLOT_WARPS_PER_SM overrides the resident warps per SM
             if (const char *env = std::getenv("IMIN_SLOT_WARPS_PER_SM")) {
                 const long v = std::strtol(env, nullptr, 10);
@@ -257,11 +323,8 @@ struct Runner {
             c.warps = ctx->num_sms * per_sm;
         }
         // never use more than half of the free device memory for slots
-        size_t freeb = 0, totalb = 0;
-        cudaMemGetInfo(&freeb, &totalb);
-        size_t avail = freeb / 2;
-        if (ctx->budget)
-            avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
+        size_t freeb = 0;
+        const size_t avail = slot_avail(&freeb);
         const size_t per = c.bytes_per_slot();
         size_t maxw = per ? avail / per : 0;
         maxw = maxw / 8 * 8;
@@ -277,8 +340,8 @@ struct Runner {
     // so the arena is only wiped when its layout changes.
     void prepare_slots(DBuf &arena, const SlotCfg &cfg, size_t &layout)
     {
-        const size_t bytes = cfg.bytes_per_slot() * (size_t)cfg.warps;
-        const size_t key = cfg.bytes_per_slot() * 1315423911u + (size_t)cfg.warps;
+        const size_t bytes = cfg.bytes_per_slot() * (size_t)cfg.slots();
+        const size_t key = cfg.bytes_per_slot() * 1315423911u + (size_t)cfg.slots();
         const void *before = arena.p;
         if (arena.p && arena.bytes < bytes) arena.release();   // never hold two arenas at once
         arena.ensure(ctx, bytes, false, true);
@@ -333,6 +396,8 @@ struct Runner {
             o.deferred = defer.as<uint32_t>() + doff[i];
             o.deferred_cap = T[i]->count;
         }
+        for (int i = 0; i < n; ++i)
+            if (!gref || T[i]->g->n > gref->n) gref = T[i]->g;
         SlotCfg cfg = cfg_for(flags, nmax, mmax, nSmax, false);
         DBuf &arena = cfg.lower ? ctx->slots_lower : ctx->slots;
         size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
@@ -414,6 +479,88 @@ struct Runner {
 };
 
 // ---------------------------------------------------------------------------
+// Autotuner: the launch configuration of reach-only worlds (the frontier tile = CTA
+// size, worlds per SM, where the visited bitmap lives, or the warp-per-world kernel)
+// is chosen per graph by timing a short probe of each candidate on the first query
+// that reaches the graph.  The probe draws worlds of a tag no solve uses and its
+// outputs are discarded, so it changes no result.  IMIN_AUTOTUNE=0 keeps the
+// default (one 1024-thread CTA per world).
+// ---------------------------------------------------------------------------
+void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
+{
+    if (g->tuned_ctas != 0) return;
+    if (const char *env = std::getenv("IMIN_AUTOTUNE"))
+        if (env[0] == '0') return;
+    const size_t words = ((size_t)g->n + 31) / 32;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    cudaGetLastError();
+    struct Cand {
+        int bd, ctas;
+        bool smem;
+        int warp_per_sm;   // > 0: warp-per-world kernel
+    };
+    std::vector<Cand> cands;
+    for (int bd : {256, 512, 1024})
+        for (int sm = 1; sm >= 0; --sm) {
+            const bool smem = sm == 1;
+            if (smem && words * 4 + cta_static_smem(bd) + 1024 > (size_t)optin) continue;
+            const int nb = cta_blocks_per_sm(bd, smem, words);
+            if (nb <= 0) continue;
+            cands.push_back(Cand{bd, ctx->num_sms * nb, smem, 0});
+        }
+    cands.push_back(Cand{0, 0, false, 32});
+    DBuf spread;
+    Runner probe_runner(ctx);
+    double best = 1e30;
+    Cand pick = cands.front();
+    for (const Cand &cd : cands) {
+        SlotCfg c;
+        c.bm_words = words;
+        if (cd.warp_per_sm) {
+            g->tuned_ctas = -cd.warp_per_sm;
+            probe_runner.force = nullptr;
+        } else {
+            c.ctas = cd.ctas;
+            c.cta_threads = cd.bd;
+            c.smem_bm = cd.smem;
+            c.qcap = g->n + 1;
+            c.warps = cd.ctas * (cd.bd / 32);
+            probe_runner.force = &c;
+        }
+        const uint32_t concurrent = cd.warp_per_sm ? (uint32_t)(ctx->num_sms * cd.warp_per_sm)
+                                                   : (uint32_t)cd.ctas;
+        // three waves of worlds, after one untimed wave that loads the kernel
+        const uint32_t worlds = std::min<uint32_t>(std::max<uint32_t>(3 * concurrent, 2048), 32768);
+        double per_world = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            TaskRun t;
+            t.g = g;
+            t.q = qdev(q, 0x5eedull, 0xFFFFFFF0u, (uint32_t)pass);
+            t.first = 0;
+            t.count = pass == 0 ? std::min<uint32_t>(concurrent, 1024) : worlds;
+            std::vector<TaskRun *> tp{&t};
+            const double before = probe_runner.kernel_ms;
+            probe_runner.gref = g;
+            probe_runner.run(tp, 0u);
+            per_world = (probe_runner.kernel_ms - before) / t.count;
+        }
+        if (per_world < best) {
+            best = per_world;
+            pick = cd;
+        }
+        g->tuned_ctas = 0;
+    }
+    if (pick.warp_per_sm) {
+        g->tuned_ctas = -pick.warp_per_sm;
+    } else {
+        g->tuned_ctas = pick.ctas;
+        g->tuned_bd = pick.bd;
+        g->tuned_smem = pick.smem;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Stopping-rule spread estimates (reach-only worlds with early exit), several
 // queries in one launch
 // ---------------------------------------------------------------------------
@@ -439,6 +586,8 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
     // estimate over its next range of worlds, with the threshold still missing as its
     // early-exit bound; the host scans the sizes in order to find N exactly.
     const size_t ns = specs.size();
+    for (size_t i = 0; i < ns; ++i)
+        autotune_reach(ctx, const_cast<imin_graph *>(specs[i].g), *specs[i].q);
     std::vector<double> W(ns), ups1(ns);
     std::vector<unsigned long long> T(ns), sum(ns, 0);
     std::vector<uint64_t> first(ns, 0), N(ns, 0), chunk(ns);

@@ -130,6 +130,11 @@ struct imin_graph {
     DBuf row_ptr, col, thr, in_ptr, in_src, in_eid, in_thr;
     DBuf ce;                // per 4-edge group {col x4, thr x4}: one 32-byte sector per group
     size_t ce_bytes = 0;
+    // reach-only launch configuration chosen by the autotuner (0 = not tuned yet):
+    // tuned_ctas > 0 -> CTA kernel with tuned_bd threads, tuned_smem bitmap in shared
+    // memory; tuned_ctas < 0 -> warp-per-world kernel with -tuned_ctas warps per SM
+    int tuned_ctas = 0, tuned_bd = 0;
+    bool tuned_smem = false;
     // host copies used by the controller (ON, q(v), out-degrees, V'_s)
     std::vector<int32_t> h_row_ptr, h_col;
     std::vector<uint32_t> h_thr;
@@ -154,7 +159,11 @@ struct SlotCfg {
     size_t bm_words = 0;    // 32-bit words of one visited bitmap
     bool lower = false, upper = false;
     int groups_per_lane = 2;  // U: 4-edge groups each lane has in flight per step
+    int ctas = 0;             // > 0: reach-only worlds run one per CTA (this many CTAs)
+    int cta_threads = 1024;   // CTA mode: threads per CTA (the frontier tile)
+    bool smem_bm = false;     // CTA mode: visited bitmap in shared memory
     size_t bytes_per_slot() const;
+    int slots() const { return ctas > 0 ? ctas : warps; }   // one slot per world in flight
 };
 
 // Outputs / stores written by the world kernel.
@@ -212,6 +221,13 @@ struct WTask {
 
 WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t count,
                 const uint32_t *list, const WorldOut &out);
+
+// CTA-per-world reach kernel (sampler_cta.cu)
+size_t cta_static_smem(int bd);
+size_t cta_slot_bytes(const SlotCfg &cfg);
+int cta_blocks_per_sm(int bd, bool smem_bm, size_t bm_words);
+void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t flags,
+                      const SlotCfg &cfg, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
 
 // One persistent launch over several tasks (all of the mode given by `flags`).
 // d_tasks holds the descriptors; d_claim / d_done are zeroed per-task counters.

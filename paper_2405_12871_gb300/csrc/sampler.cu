@@ -547,6 +547,7 @@ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 size_t SlotCfg::bytes_per_slot() const
 {
+    if (ctas > 0) return cta_slot_bytes(*this);
     size_t b = al16(bm_words * 4) + al16((size_t)qcap * 4);
     if (lower) {
         // loc is indexed by node id: n entries = 32 * bm_words upper bound
@@ -615,6 +616,10 @@ void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_gr
                   uint32_t *d_done)
 {
     if (ntasks <= 0) return;
+    if (cfg.ctas > 0) {
+        launch_cta_tasks(ctx, d_tasks, ntasks, flags, cfg, slot_base, d_claim, d_done);
+        return;
+    }
     KArgs a;
     a.tasks = d_tasks;
     a.ntasks = ntasks;

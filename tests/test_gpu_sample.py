@@ -96,6 +96,30 @@ def test_deferred_worlds_match(er1k, monkeypatch):
     assert_sample_equal(got, want)
 
 
+@pytest.mark.parametrize("cfg", ["warp", "256/g", "512/g", "1024/g", "256/s", "512/s", "1024/s"])
+def test_reach_launch_configurations(ctx, monkeypatch, cfg):
+    """Reach-only worlds give the same bits under every launch configuration the
+    autotuner may pick: warp-per-world, or a CTA per world of 256/512/1024 threads
+    with the visited bitmap in global (g) or shared (s) memory."""
+    g = synth.chung_lu(30_000, 12.0, 2.1, seed=11)
+    S = synth.seeds_top_outdeg(g, 30, 0.01, seed=12)
+    rng = np.random.default_rng(13)
+    B = rng.choice(np.setdiff1d(np.arange(g.n), S), 40, replace=False)
+    if cfg == "warp":
+        monkeypatch.setenv("IMIN_REACH_CTA", "0")
+    else:
+        bd, where = cfg.split("/")
+        monkeypatch.setenv("IMIN_REACH_BD", bd)
+        monkeypatch.setenv("IMIN_REACH_SMEM", "1" if where == "s" else "0")
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    for blocked, theta, first in (([], 700, 0), (B, 500, 77_777)):
+        got = G.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=1, per_world=True)
+        want = og.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=1, per_world=True)
+        assert_sample_equal(got, want)
+    G.free()
+
+
 def test_small_chung_lu_hubs(ctx):
     g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
     S = synth.seeds_top_outdeg(g, 20, 0.01, seed=4)
