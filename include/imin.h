@@ -103,6 +103,17 @@ int imin_load_graph(imin_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr,
 /* Release a graph.  NULL is ignored. */
 void imin_free_graph(imin_graph *g);
 
+/* The launch configuration the library's autotuner chose for reach-only worlds on
+ * this graph (performance only: every configuration gives the same counts).  The
+ * first stopping-rule estimate on a graph times a short probe of each configuration
+ * and keeps the fastest; graphs of the same shape reuse the choice.
+ *   out[0]  > 0: CTAs of the CTA-per-world kernel; < 0: minus the warps per SM of
+ *           the warp-per-world kernel; 0: not tuned yet (defaults apply)
+ *   out[1]  threads per CTA, out[2] CTAs per SM the kernel was compiled for,
+ *   out[3]  1 if the visited bitmap lives in shared memory.
+ * Errors: IMIN_EINVAL (NULL argument). */
+int imin_graph_tuning(const imin_graph *g, int32_t out[4]);
+
 /* Options of imin_sample.  Worlds [first_sample, first_sample + theta) of the
  * stream (key, tag, inst) are drawn. */
 typedef struct imin_sample_opts {

@@ -21,7 +21,7 @@ VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
            "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc",
            "imin_solve_batch", "imin_server_start", "imin_server_submit", "imin_server_poll",
-           "imin_server_stop"]
+           "imin_server_stop", "imin_graph_tuning"]
 NOALLOC_MAX_NODES = 2_000_000
 
 
@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
     L.imin_load_graph.restype = C.c_int
     L.imin_free_graph.argtypes = [C.c_void_p]
     L.imin_free_graph.restype = None
+    L.imin_graph_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    L.imin_graph_tuning.restype = C.c_int
     L.imin_sample.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), C.c_int32,
                               C.c_uint64, P(SampleOpts), P(SampleOut)]
     L.imin_sample.restype = C.c_int
@@ -328,6 +330,14 @@ class Graph:
 
     def solve(self, S, k, eps, delta, **kw):
         return imin_solve(self.ctx.h, self.h, S, k, eps, delta, **kw)
+
+    def tuning(self):
+        """The autotuner's reach-only launch choice: dict(ctas, threads, minb, smem_bitmap)."""
+        out = (C.c_int32 * 4)()
+        rc = load().imin_graph_tuning(self.h, out)
+        if rc != IMIN_OK:
+            raise IminError(rc, "imin_graph_tuning: " + load().imin_strerror(rc).decode())
+        return dict(ctas=out[0], threads=out[1], minb=out[2], smem_bitmap=bool(out[3]))
 
     def free(self):
         if self.h:

@@ -269,6 +269,7 @@ struct Runner {
             if (gref && gref->tuned_ctas > 0 && !env_warp) {
                 c.smem_bm = gref->tuned_smem;
                 c.cta_threads = gref->tuned_bd;
+                c.cta_minb = gref->tuned_minb;
                 c.qcap = n + 1;
                 c.ecap = 0;
                 c.ctas = gref->tuned_ctas;
@@ -279,20 +280,28 @@ struct Runner {
                 int optin = 0;
                 cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
                 cudaGetLastError();
-                // test hooks: IMIN_REACH_BD picks the CTA size, IMIN_REACH_SMEM=0 keeps the
-                // visited bitmap in global memory
-                int bd = 1024;
+                // test hooks: IMIN_REACH_BD picks the CTA size (and IMIN_REACH_MINB the
+                // CTAs per SM it is compiled for), IMIN_REACH_SMEM=0 keeps the visited
+                // bitmap in global memory
+                int bd = 512, minb = 4;
                 if (const char *env = std::getenv("IMIN_REACH_BD")) {
                     const long v = std::strtol(env, nullptr, 10);
-                    if (v == 256 || v == 512) bd = (int)v;
+                    if (v == 256 || v == 512 || v == 1024) bd = (int)v;
+                    minb = bd == 256 ? 8 : (bd == 512 ? 4 : 2);
+                }
+                if (const char *env = std::getenv("IMIN_REACH_MINB")) {
+                    const long v = std::strtol(env, nullptr, 10);
+                    for (int i = 0; i < kNumCtaShapes; ++i)
+                        if (kCtaShapes[i][0] == bd && kCtaShapes[i][1] == v) minb = (int)v;
                 }
                 c.smem_bm = c.bm_words * 4 + cta_static_smem(bd) + 1024 <= (size_t)optin;
                 if (const char *env = std::getenv("IMIN_REACH_SMEM"))
                     if (env[0] == '0') c.smem_bm = false;
                 c.cta_threads = bd;
+                c.cta_minb = minb;
                 c.qcap = n + 1;
                 c.ecap = 0;
-                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, c.smem_bm, c.bm_words));
+                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, minb, c.smem_bm, c.bm_words));
                 c.warps = c.ctas * (bd / 32);
                 return cap_ctas(c);
             }
@@ -486,31 +495,65 @@ struct Runner {
 // outputs are discarded, so it changes no result.  IMIN_AUTOTUNE=0 keeps the
 // default (one 1024-thread CTA per world).
 // ---------------------------------------------------------------------------
+// graphs of the same shape (n, m and 64 sampled row offsets) share a tuning
+uint64_t graph_signature(const imin_graph *g)
+{
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)g->n ^ ((uint64_t)g->m << 20);
+    const size_t len = g->h_row_ptr.size();
+    for (int i = 0; i < 64 && len; ++i) {
+        h ^= (uint64_t)(uint32_t)g->h_row_ptr[(size_t)i * (len - 1) / 63];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
 void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
 {
     if (g->tuned_ctas != 0) return;
     if (const char *env = std::getenv("IMIN_AUTOTUNE"))
         if (env[0] == '0') return;
+    const uint64_t sig = graph_signature(g);
+    for (const imin_ctx::TuneEntry &te : ctx->tune_cache)
+        if (te.sig == sig && te.n == g->n && te.m == g->m) {
+            g->tuned_ctas = te.ctas;
+            g->tuned_bd = te.bd;
+            g->tuned_minb = te.minb;
+            g->tuned_smem = te.smem;
+            return;
+        }
     const size_t words = ((size_t)g->n + 31) / 32;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     cudaGetLastError();
     struct Cand {
-        int bd, ctas;
+        int bd, minb, ctas;
         bool smem;
         int warp_per_sm;   // > 0: warp-per-world kernel
     };
     std::vector<Cand> cands;
-    for (int bd : {256, 512, 1024})
+    for (int i = 0; i < kNumCtaShapes; ++i)
         for (int sm = 1; sm >= 0; --sm) {
+            const int bd = kCtaShapes[i][0], minb = kCtaShapes[i][1];
             const bool smem = sm == 1;
             if (smem && words * 4 + cta_static_smem(bd) + 1024 > (size_t)optin) continue;
-            const int nb = cta_blocks_per_sm(bd, smem, words);
+            const int nb = std::min(minb, cta_blocks_per_sm(bd, minb, smem, words));
             if (nb <= 0) continue;
-            cands.push_back(Cand{bd, ctx->num_sms * nb, smem, 0});
+            // a shape compiled for more CTAs per SM than fit is the same launch as a
+            // smaller one with fewer registers: skip it
+            if (nb < minb && minb > 1) {
+                bool dup = false;
+                for (int k = 0; k < kNumCtaShapes; ++k)
+                    dup |= kCtaShapes[k][0] == bd && kCtaShapes[k][1] < minb && kCtaShapes[k][1] >= nb;
+                if (dup) continue;
+            }
+            cands.push_back(Cand{bd, minb, ctx->num_sms * nb, smem, 0});
         }
-    cands.push_back(Cand{0, 0, false, 32});
-    DBuf spread;
+    cands.push_back(Cand{0, 0, 0, false, 32});
+    // Each candidate is timed on W and on 2W worlds; the difference over W is its cost
+    // per world in a long launch, free of the launch's fill and drain (the solve's
+    // launches hold thousands of worlds per CTA).  W is two waves of the candidate.
+    uint32_t widest = 0;
+    for (const Cand &cd : cands) widest = std::max<uint32_t>(widest, (uint32_t)cd.ctas);
     Runner probe_runner(ctx);
     double best = 1e30;
     Cand pick = cands.front();
@@ -523,6 +566,7 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
         } else {
             c.ctas = cd.ctas;
             c.cta_threads = cd.bd;
+            c.cta_minb = cd.minb;
             c.smem_bm = cd.smem;
             c.qcap = g->n + 1;
             c.warps = cd.ctas * (cd.bd / 32);
@@ -530,21 +574,22 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
         }
         const uint32_t concurrent = cd.warp_per_sm ? (uint32_t)(ctx->num_sms * cd.warp_per_sm)
                                                    : (uint32_t)cd.ctas;
-        // three waves of worlds, after one untimed wave that loads the kernel
-        const uint32_t worlds = std::min<uint32_t>(std::max<uint32_t>(3 * concurrent, 2048), 32768);
-        double per_world = 0.0;
-        for (int pass = 0; pass < 2; ++pass) {
+        const uint32_t W = std::min<uint32_t>(std::max<uint32_t>(2 * std::max(concurrent, widest), 2048), 16384);
+        // an untimed wave loads the kernel, then W and 2W worlds
+        double ms[3] = {0.0, 0.0, 0.0};
+        for (int pass = 0; pass < 3; ++pass) {
             TaskRun t;
             t.g = g;
             t.q = qdev(q, 0x5eedull, 0xFFFFFFF0u, (uint32_t)pass);
             t.first = 0;
-            t.count = pass == 0 ? std::min<uint32_t>(concurrent, 1024) : worlds;
+            t.count = pass == 0 ? std::min<uint32_t>(concurrent, 1024) : (uint32_t)pass * W;
             std::vector<TaskRun *> tp{&t};
             const double before = probe_runner.kernel_ms;
             probe_runner.gref = g;
             probe_runner.run(tp, 0u);
-            per_world = (probe_runner.kernel_ms - before) / t.count;
+            ms[pass] = probe_runner.kernel_ms - before;
         }
+        const double per_world = ms[2] > ms[1] ? (ms[2] - ms[1]) / W : ms[2] / (2.0 * W);
         if (per_world < best) {
             best = per_world;
             pick = cd;
@@ -556,8 +601,11 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
     } else {
         g->tuned_ctas = pick.ctas;
         g->tuned_bd = pick.bd;
+        g->tuned_minb = pick.minb;
         g->tuned_smem = pick.smem;
     }
+    ctx->tune_cache.push_back(imin_ctx::TuneEntry{sig, g->n, g->m, g->tuned_ctas, g->tuned_bd, g->tuned_minb,
+                                                  g->tuned_smem});
 }
 
 // ---------------------------------------------------------------------------
@@ -1515,6 +1563,16 @@ void imin_free_graph(imin_graph *g)
     if (!g) return;
     cudaSetDevice(g->ctx->device);
     delete g;
+}
+
+int imin_graph_tuning(const imin_graph *g, int32_t out[4])
+{
+    if (!g || !out) return IMIN_EINVAL;
+    out[0] = g->tuned_ctas;
+    out[1] = g->tuned_bd;
+    out[2] = g->tuned_minb;
+    out[3] = g->tuned_smem ? 1 : 0;
+    return IMIN_OK;
 }
 
 int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *blocked, int32_t nB,

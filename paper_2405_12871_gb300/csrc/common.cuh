@@ -111,6 +111,15 @@ struct imin_ctx {
     size_t l2_window_bytes = 0, l2_persist_bytes = 0;
     size_t prev_persist_limit = 0;
     bool persist_set = false;
+    // reach-only launch configurations chosen by the autotuner, by graph shape
+    struct TuneEntry {
+        uint64_t sig;
+        int32_t n;
+        int64_t m;
+        int ctas, bd, minb;
+        bool smem;
+    };
+    std::vector<TuneEntry> tune_cache;
     DBuf misc;              // small per-call device scalars
     DBuf hostpin_dummy;
     unsigned long long *h_misc = nullptr;  // pinned host mirror of `misc` scalars
@@ -131,9 +140,10 @@ struct imin_graph {
     DBuf ce;                // per 4-edge group {col x4, thr x4}: one 32-byte sector per group
     size_t ce_bytes = 0;
     // reach-only launch configuration chosen by the autotuner (0 = not tuned yet):
-    // tuned_ctas > 0 -> CTA kernel with tuned_bd threads, tuned_smem bitmap in shared
-    // memory; tuned_ctas < 0 -> warp-per-world kernel with -tuned_ctas warps per SM
-    int tuned_ctas = 0, tuned_bd = 0;
+    // tuned_ctas > 0 -> CTA kernel with tuned_bd threads (compiled for tuned_minb CTAs
+    // per SM), tuned_smem bitmap in shared memory; tuned_ctas < 0 -> warp-per-world
+    // kernel with -tuned_ctas warps per SM
+    int tuned_ctas = 0, tuned_bd = 0, tuned_minb = 0;
     bool tuned_smem = false;
     // host copies used by the controller (ON, q(v), out-degrees, V'_s)
     std::vector<int32_t> h_row_ptr, h_col;
@@ -161,6 +171,7 @@ struct SlotCfg {
     int groups_per_lane = 2;  // U: 4-edge groups each lane has in flight per step
     int ctas = 0;             // > 0: reach-only worlds run one per CTA (this many CTAs)
     int cta_threads = 1024;   // CTA mode: threads per CTA (the frontier tile)
+    int cta_minb = 1;         // CTA mode: CTAs per SM the kernel is compiled for
     bool smem_bm = false;     // CTA mode: visited bitmap in shared memory
     size_t bytes_per_slot() const;
     int slots() const { return ctas > 0 ? ctas : warps; }   // one slot per world in flight
@@ -222,10 +233,13 @@ struct WTask {
 WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t count,
                 const uint32_t *list, const WorldOut &out);
 
-// CTA-per-world reach kernel (sampler_cta.cu)
+// CTA-per-world reach kernel (reach_cta.cuh, sampler_cta.cu): the compiled shapes
+// {threads per CTA, CTAs per SM}
+extern const int kCtaShapes[][2];
+extern const int kNumCtaShapes;
 size_t cta_static_smem(int bd);
 size_t cta_slot_bytes(const SlotCfg &cfg);
-int cta_blocks_per_sm(int bd, bool smem_bm, size_t bm_words);
+int cta_blocks_per_sm(int bd, int minb, bool smem_bm, size_t bm_words);
 void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t flags,
                       const SlotCfg &cfg, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
 

@@ -96,27 +96,71 @@ def test_deferred_worlds_match(er1k, monkeypatch):
     assert_sample_equal(got, want)
 
 
-@pytest.mark.parametrize("cfg", ["warp", "256/g", "512/g", "1024/g", "256/s", "512/s", "1024/s"])
-def test_reach_launch_configurations(ctx, monkeypatch, cfg):
-    """Reach-only worlds give the same bits under every launch configuration the
-    autotuner may pick: warp-per-world, or a CTA per world of 256/512/1024 threads
-    with the visited bitmap in global (g) or shared (s) memory."""
+@pytest.fixture(scope="module")
+def hubs30k():
+    """A 30,000-node Chung-Lu graph with hubs (many nodes above the hub threshold of
+    the CTA kernel), its seeds, 40 blocked nodes and the oracle's reach-only worlds."""
     g = synth.chung_lu(30_000, 12.0, 2.1, seed=11)
     S = synth.seeds_top_outdeg(g, 30, 0.01, seed=12)
     rng = np.random.default_rng(13)
     B = rng.choice(np.setdiff1d(np.arange(g.n), S), 40, replace=False)
+    og = oracle.OracleGraph.from_graph(g)
+    cases = (([], 700, 0), (B, 500, 77_777))
+    want = [og.sample(S, b, theta=t, key=3, tag=5, first=f, mode=1, per_world=True) for b, t, f in cases]
+    return g, S, cases, want
+
+
+REACH_CONFIGS = ["warp"] + [f"{bd}x{mb}/{w}" for bd, mb in ((256, 4), (256, 8), (512, 2), (512, 4),
+                                                            (1024, 1), (1024, 2)) for w in "gs"]
+
+
+@pytest.mark.parametrize("cfg", REACH_CONFIGS)
+def test_reach_launch_configurations(ctx, monkeypatch, hubs30k, cfg):
+    """Reach-only worlds give the same bits under every launch configuration the
+    autotuner may pick: warp-per-world, or a CTA per world of 256/512/1024 threads
+    compiled for a given number of CTAs per SM, with the visited bitmap in global (g)
+    or shared (s) memory."""
+    g, S, cases, want = hubs30k
     if cfg == "warp":
         monkeypatch.setenv("IMIN_REACH_CTA", "0")
     else:
-        bd, where = cfg.split("/")
+        shape, where = cfg.split("/")
+        bd, mb = shape.split("x")
         monkeypatch.setenv("IMIN_REACH_BD", bd)
+        monkeypatch.setenv("IMIN_REACH_MINB", mb)
         monkeypatch.setenv("IMIN_REACH_SMEM", "1" if where == "s" else "0")
     G = ctx.load_graph(g)
-    og = oracle.OracleGraph.from_graph(g)
-    for blocked, theta, first in (([], 700, 0), (B, 500, 77_777)):
+    for (blocked, theta, first), w in zip(cases, want):
         got = G.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=1, per_world=True)
-        want = og.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=1, per_world=True)
-        assert_sample_equal(got, want)
+        assert_sample_equal(got, w)
+    G.free()
+
+
+@pytest.mark.parametrize("cfg", ["512x4/g", "1024x1/s", "256x8/s"])
+def test_reach_many_hubs_in_one_level(ctx, monkeypatch, cfg):
+    """400 hubs in one BFS level: more than the CTA kernel stages for its hub pass,
+    so the rest are expanded by the warp that met them."""
+    rng = np.random.default_rng(21)
+    nh, deg, ns = 400, 160, 8
+    n = ns + nh + 30_000
+    hubs = np.arange(ns, ns + nh)
+    src = [np.repeat(np.arange(ns), nh), np.repeat(hubs, deg)]
+    dst = [np.tile(hubs, ns), rng.integers(ns + nh, n, nh * deg)]
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    prob = np.where(src < ns, 1.0, 0.3).astype(np.float32)
+    g = synth.csr_from_edges(n, src, dst, prob)
+    shape, where = cfg.split("/")
+    bd, mb = shape.split("x")
+    monkeypatch.setenv("IMIN_REACH_BD", bd)
+    monkeypatch.setenv("IMIN_REACH_MINB", mb)
+    monkeypatch.setenv("IMIN_REACH_SMEM", "1" if where == "s" else "0")
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    S = np.arange(ns)
+    got = G.sample(S, theta=200, key=9, tag=2, mode=1, per_world=True)
+    want = og.sample(S, theta=200, key=9, tag=2, mode=1, per_world=True)
+    assert_sample_equal(got, want)
+    assert want["total_spread"] > 200 * (ns + nh)
     G.free()
 
 

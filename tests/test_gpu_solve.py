@@ -103,3 +103,30 @@ def test_stopping_rule_in_many_chunks(ctx, monkeypatch):
     compare(got, og.solve(S, **kw))
     assert got["n_spread"] > 5 * 997
     G.free()
+
+
+def test_autotuner_choice_is_cached_and_changes_nothing(ctx, monkeypatch):
+    """The reach-only launch autotuner runs on the first stopping-rule estimate of a
+    graph, its choice is reused by a second handle of the same graph, and a solve with
+    the autotuner off gives the same bits."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=5)
+    S = synth.seeds_top_outdeg(g, 15, 0.01, seed=6)
+    kw = dict(k=6, eps=0.3, delta=0.05, key=2)
+    G = ctx.load_graph(g)
+    assert G.tuning()["ctas"] == 0
+    first = G.solve(S, **kw)
+    t = G.tuning()
+    assert t["ctas"] != 0
+    if t["ctas"] > 0:
+        assert t["threads"] in (256, 512, 1024) and t["minb"] >= 1
+    H = ctx.load_graph(g)
+    again = H.solve(S, **kw)
+    assert H.tuning() == t
+    compare(again, first)
+    monkeypatch.setenv("IMIN_AUTOTUNE", "0")
+    K = ctx.load_graph(g)
+    off = K.solve(S, **kw)
+    assert K.tuning()["ctas"] == 0
+    compare(off, first)
+    for x in (G, H, K):
+        x.free()
