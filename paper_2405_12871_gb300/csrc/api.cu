@@ -263,8 +263,14 @@ struct Runner {
         // bitmap in shared memory when n bits fit; the autotuner's choice for the graph
         // wins when there is one (IMIN_REACH_CTA=0 selects the warp-per-world kernel)
         const char *cta_env = std::getenv("IMIN_REACH_CTA");
-        if (!c.lower && !c.upper && !big) {
-            if (force) return cap_ctas(*force);   // autotuner probe
+        const char *upper_env = std::getenv("IMIN_UPPER_CTA");
+        const bool upper_cta = c.upper && !(upper_env && upper_env[0] == '0');
+        if (!c.lower && (!c.upper || upper_cta) && !big) {
+            if (force) {   // autotuner probe
+                SlotCfg f = *force;
+                f.upper = c.upper;
+                return cap_ctas(f);
+            }
             const bool env_warp = cta_env && cta_env[0] == '0';
             if (gref && gref->tuned_ctas > 0 && !env_warp) {
                 c.smem_bm = gref->tuned_smem;
@@ -301,7 +307,7 @@ struct Runner {
                 c.cta_minb = minb;
                 c.qcap = n + 1;
                 c.ecap = 0;
-                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, minb, c.smem_bm, c.bm_words));
+                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, minb, c.smem_bm, c.upper, c.bm_words));
                 c.warps = c.ctas * (bd / 32);
                 return cap_ctas(c);
             }
@@ -536,7 +542,7 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
             const int bd = kCtaShapes[i][0], minb = kCtaShapes[i][1];
             const bool smem = sm == 1;
             if (smem && words * 4 + cta_static_smem(bd) + 1024 > (size_t)optin) continue;
-            const int nb = std::min(minb, cta_blocks_per_sm(bd, minb, smem, words));
+            const int nb = std::min(minb, cta_blocks_per_sm(bd, minb, smem, false, words));
             if (nb <= 0) continue;
             // a shape compiled for more CTAs per SM than fit is the same launch as a
             // smaller one with fewer registers: skip it
@@ -728,6 +734,12 @@ SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double b
 // ---------------------------------------------------------------------------
 // Collections: CP records (C1, C2) and LRR sets (L1, L2), appended together
 // ---------------------------------------------------------------------------
+bool store_tight()
+{
+    const char *env = std::getenv("IMIN_STORE_TIGHT");
+    return env && env[0] == '1';
+}
+
 void cp_reserve(imin_ctx *ctx, CpStore &c, unsigned long long need)
 {
     if (need <= c.cap && c.node.p) return;
@@ -770,7 +782,7 @@ void sample_cp(imin_ctx *ctx, std::vector<CpJob> &jobs)
         }
         const unsigned long long est =
             (unsigned long long)((double)(J.to - J.from) * std::max(J.per_world, 1.0) * 1.25) + 4096;
-        cp_reserve(ctx, c, (unsigned long long)c.count + est);
+        cp_reserve(ctx, c, (unsigned long long)c.count + (store_tight() ? 1 : est));
         TaskRun &t = tr[i];
         t.g = J.g;
         t.q = qdev(*J.q, J.key, J.tag, J.inst);
@@ -866,9 +878,14 @@ void sample_lrr(imin_ctx *ctx, std::vector<LrrJob> &jobs)
             IM_CUDA(cudaMemsetAsync(L.cursor.p, 0, 8, ctx->stream));
             L.elems = 0;
         }
-        // start from the average set size seen so far (64 per world before any is known)
+        // start from the average set size seen so far (64 per world before any is known);
+        // test hook: IMIN_STORE_TIGHT=1 starts from almost nothing, so that most worlds
+        // take the store-growth (deferred world) path
         const unsigned long long per = L.nsets ? L.elems / L.nsets + 1 : 64;
-        lrr_reserve(ctx, L, L.elems + (J.to - J.from) * per * 2 + 65536, J.to);
+        if (store_tight())
+            lrr_reserve(ctx, L, L.elems + 1, J.to);
+        else
+            lrr_reserve(ctx, L, L.elems + (J.to - J.from) * per * 2 + 65536, J.to);
         TaskRun &t = tr[i];
         t.g = J.g;
         t.q = qdev(*J.q, J.key, J.tag, J.inst);

@@ -1,21 +1,27 @@
-// reach_cta.cuh -- reach-only worlds with one CTA per world (kernel template).
+// reach_cta.cuh -- one CTA per world: reach-only worlds and upper-bound (LRR) worlds.
 //
 // A CTA traverses one live-edge world (Sec. 2.1: coins by Philox on (world, edge),
-// blocked nodes pre-marked as visited) level by level.  Per level:
+// blocked nodes pre-marked as visited) breadth first, level by level.  Per level:
 //   phase 1  warps claim 32-node slices of the frontier from a shared counter.  A
-//            warp scans its slice's 4-edge group counts with shuffles, and each
-//            pass gives one group to each lane.  A lane finds its node by a
-//            five-step shuffle search over the warp's running counts, so there is
-//            no block-wide scan and no barrier inside the level.  A node with more
-//            than BIG_GROUPS groups (a hub) goes to a shared list instead.
-//   phase 2  the hubs' groups are cut into pieces of PIECE groups; warps claim
-//            pieces, so a hub's edges spread over the whole CTA.
-// A pass loads each lane's group (one 32-byte record: 4 targets, 4 coin thresholds),
-// draws its four coins with one Philox call, and keeps the in-range live edges.  The
-// warp stages them in shared memory, and each lane then claims one target in the
-// visited bitmap (shared or global) with an atomic OR.  Newly visited nodes are
-// appended to the queue with one shared atomic per warp ballot.  Every count equals
-// that of the warp-per-world kernel, because the result of a world is a set.
+//            warp scans its slice's work-item counts with shuffles, and each pass gives
+//            one item to each lane.  A lane finds its node by a five-step shuffle
+//            search over the warp's running counts, so there is no block-wide scan and
+//            no barrier inside the level.  A node with more than BIG items (a hub)
+//            goes to a shared list instead.
+//   phase 2  the hubs' items are cut into pieces of PIECE items; warps claim pieces,
+//            so a hub's edges spread over the whole CTA.
+// Forward, an item is a 4-edge group (one 32-byte record: 4 targets, 4 coin
+// thresholds; one Philox call draws its four coins).  In reverse, an item is one
+// in-edge.  A pass keeps each lane's live in-range edges; the warp stages them in
+// shared memory, and each lane then claims one target in the visited bitmap (shared
+// or global) with an atomic OR.  Newly visited nodes are appended to the queue with
+// one shared atomic per warp ballot.
+//
+// Upper-bound worlds (Sec. 5.2, the Global Sampling bound) then draw the target t
+// uniformly from V'_s.  If the forward pass reached t, they run the reverse BFS from
+// t over live in-edges whose source the forward pass reached and which is not a seed
+// (nor blocked).  That set is the world's LRR set; it is credited and stored.  Every
+// count equals that of the warp-per-world kernel: a world's results are sets.
 #pragma once
 
 #include "common.cuh"
@@ -30,13 +36,14 @@ struct CArgs {
     char *slot_base;
     size_t slot_bytes;
     size_t bm_words;
-    size_t off_queue;
+    size_t off_queue, off_bm2, off_q2;
+    uint32_t flags;
 };
 
-constexpr int BIG_GROUPS = 32;   // nodes with more groups are expanded in phase 2
-constexpr int PIECE = 128;       // groups per phase-2 claim
-constexpr int BIGCAP = 256;      // hubs staged per level (further hubs stay in phase 1)
-constexpr int CAND = 128;        // per-warp staging: 32 lanes x 4 edges
+constexpr int BIG = 32;       // nodes with more items are expanded in phase 2
+constexpr int PIECE = 128;    // items per phase-2 claim
+constexpr int BIGCAP = 256;   // hubs staged per level (further hubs stay in phase 1)
+constexpr int CAND = 128;     // per-warp staging: 32 lanes x 4 edges
 
 template <int BD>
 struct Shared {
@@ -46,14 +53,9 @@ struct Shared {
     int slice[2], nbig[2], piece[2], app[2];   // per level parity
     int task;
     uint32_t rel;
+    int target;
     unsigned long long edges;
-};
-
-struct World {
-    const uint4 *ce;
-    uint32_t *bm;
-    int32_t *Q;
-    uint32_t j, tag, inst, klo, khi;
+    unsigned long long sbase;
 };
 
 __device__ __forceinline__ uint4 philox10_w(uint4 c, uint32_t k0, uint32_t k1)
@@ -70,28 +72,82 @@ __device__ __forceinline__ uint4 philox10_w(uint4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
-// One pass: each active lane expands group g of a node whose edges are [ob, oe).
-// Must be called by all 32 lanes of the warp.  Appends go to Q[tail + ...] through
-// the level's append counter.
+struct Coins {
+    uint32_t j, tag, inst, klo, khi;
+};
+
+// Forward items: the 4-edge groups of a node's out-edges [b, e).
+struct Fwd {
+    static constexpr bool kCountEdges = true;   // the scanned edges are reported
+    const int32_t *row_ptr;
+    const uint4 *ce;
+    __device__ __forceinline__ void range(int u, int &b, int &e) const
+    {
+        b = row_ptr[u];
+        e = row_ptr[u + 1];
+    }
+    __device__ __forceinline__ static int first(int b) { return b >> 2; }
+    __device__ __forceinline__ static int count(int b, int e) { return e > b ? ((e + 3) >> 2) - (b >> 2) : 0; }
+    // live in-range edges of group g as a 4-bit mask, their targets in c4
+    __device__ __forceinline__ uint32_t live(int g, int ob, int oe, const Coins &K, int4 &c4) const
+    {
+        const int4 *p = reinterpret_cast<const int4 *>(ce + 2 * (size_t)g);
+        c4 = __ldg(p);
+        const uint4 t4 = __ldg(reinterpret_cast<const uint4 *>(p + 1));
+        const uint4 w = philox10_w(make_uint4((uint32_t)g, K.j, K.tag, K.inst), K.klo, K.khi);
+        uint32_t m = (uint32_t)((w.x >> 8) < t4.x) | ((uint32_t)((w.y >> 8) < t4.y) << 1) |
+                     ((uint32_t)((w.z >> 8) < t4.z) << 2) | ((uint32_t)((w.w >> 8) < t4.w) << 3);
+        // edges of the group outside [ob, oe) belong to neighbouring nodes
+        const int e0 = g << 2;
+        if (e0 < ob) m &= 0xFu << (ob - e0);
+        if (e0 + 4 > oe) m &= (1u << (oe - e0)) - 1u;
+        return m;
+    }
+};
+
+// Reverse items: the in-edges [b, e) of a node; an in-edge (u, v) is followed when u
+// was reached by the forward pass, u is neither a seed nor blocked, and its coin (the
+// forward edge's) is live.
 template <bool SMEM_BM>
-__device__ __forceinline__ void expand_groups(bool act, int g, int ob, int oe, const World &W,
-                                              int *cand, int *app, int tail, int lane,
-                                              uint32_t lt_mask)
+struct Rev {
+    static constexpr bool kCountEdges = false;
+    const int32_t *in_ptr, *in_src, *in_eid;
+    const uint32_t *in_thr;
+    const uint32_t *fwd_bm, *seed_bm, *blocked_bm;
+    __device__ __forceinline__ void range(int v, int &b, int &e) const
+    {
+        b = in_ptr[v];
+        e = in_ptr[v + 1];
+    }
+    __device__ __forceinline__ static int first(int b) { return b; }
+    __device__ __forceinline__ static int count(int b, int e) { return e - b; }
+    __device__ __forceinline__ uint32_t live(int idx, int, int, const Coins &K, int4 &c4) const
+    {
+        const int u = __ldg(in_src + idx);
+        const uint32_t fw = SMEM_BM ? fwd_bm[u >> 5] : __ldcg(fwd_bm + (u >> 5));
+        if (!((fw >> (u & 31)) & 1u)) return 0;
+        if ((__ldg(seed_bm + (u >> 5)) >> (u & 31)) & 1u) return 0;
+        if (blocked_bm && ((__ldg(blocked_bm + (u >> 5)) >> (u & 31)) & 1u)) return 0;
+        const int eid = __ldg(in_eid + idx);
+        const uint32_t th = __ldg(in_thr + idx);
+        const uint4 w = philox10_w(make_uint4((uint32_t)eid >> 2, K.j, K.tag, K.inst), K.klo, K.khi);
+        const int c = eid & 3;
+        const uint32_t word = c == 0 ? w.x : (c == 1 ? w.y : (c == 2 ? w.z : w.w));
+        c4.x = u;
+        return (word >> 8) < th ? 1u : 0u;
+    }
+};
+
+// One pass over one item per lane (act): stage the live targets of the warp, claim
+// them in bm and append the new ones to Q[tail + ...].  All 32 lanes must call it.
+template <class Op>
+__device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int oe, const Coins &K,
+                                     uint32_t *bm, int32_t *Q, int *cand, int *app, int tail, int lane,
+                                     uint32_t lt_mask)
 {
     uint32_t live = 0;
     int4 c4 = make_int4(0, 0, 0, 0);
-    if (act) {
-        const int4 *p = reinterpret_cast<const int4 *>(W.ce + 2 * (size_t)g);
-        c4 = __ldg(p);
-        const uint4 t4 = __ldg(reinterpret_cast<const uint4 *>(p + 1));
-        const uint4 w = philox10_w(make_uint4((uint32_t)g, W.j, W.tag, W.inst), W.klo, W.khi);
-        live = (uint32_t)((w.x >> 8) < t4.x) | ((uint32_t)((w.y >> 8) < t4.y) << 1) |
-               ((uint32_t)((w.z >> 8) < t4.z) << 2) | ((uint32_t)((w.w >> 8) < t4.w) << 3);
-        // edges of the group outside [ob, oe) belong to neighbouring nodes
-        const int e0 = g << 2;
-        if (e0 < ob) live &= 0xFu << (ob - e0);
-        if (e0 + 4 > oe) live &= (1u << (oe - e0)) - 1u;
-    }
+    if (act) live = op.live(it, ob, oe, K, c4);
     const int nl = __popc(live);
     int incl = nl;
 #pragma unroll
@@ -114,7 +170,7 @@ __device__ __forceinline__ void expand_groups(bool act, int g, int ob, int oe, c
         if (k < tot) {
             v = cand[k];
             const uint32_t bit = 1u << (v & 31);
-            const uint32_t old = atomicOr(&W.bm[v >> 5], bit);
+            const uint32_t old = atomicOr(&bm[v >> 5], bit);
             fresh = !(old & bit);
         }
         const uint32_t bal = __ballot_sync(IMIN_FULL, fresh);
@@ -122,25 +178,156 @@ __device__ __forceinline__ void expand_groups(bool act, int g, int ob, int oe, c
             int base = 0;
             if (lane == 0) base = atomicAdd(app, __popc(bal));
             base = __shfl_sync(IMIN_FULL, base, 0);
-            if (fresh) W.Q[tail + base + __popc(bal & lt_mask)] = v;
+            if (fresh) Q[tail + base + __popc(bal & lt_mask)] = v;
         }
     }
     __syncwarp();
 }
 
-template <int BD, int MINB, bool SMEM_BM, bool STOP>
-__global__ void __launch_bounds__(BD, MINB) cta_reach_kernel(const CArgs a)
+// Breadth-first expansion of Q[0, tail0) until no level adds a node; returns the
+// final tail.  The caller zeroes the counters of both parities and passes a CTA
+// barrier before the call; the call ends with a CTA barrier.
+template <int BD, class Op>
+__device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, int32_t *Q, int tail0,
+                                   Shared<BD> &sh, unsigned long long &wedges)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int *const cand = sh.cand[warp];
+    int head = 0, tail = tail0, lvl = 0;
+    while (head < tail) {
+        const int p = lvl & 1;
+        if (tid == 0) sh.slice[p ^ 1] = sh.nbig[p ^ 1] = sh.piece[p ^ 1] = 0;
+        // ---- phase 1: 32-node slices, one warp each ----
+        for (;;) {
+            int sl = 0;
+            if (lane == 0) sl = atomicAdd(&sh.slice[p], 1);
+            sl = __shfl_sync(IMIN_FULL, sl, 0);
+            const int base = head + sl * 32;
+            if (base >= tail) break;
+            const int i = base + lane;
+            int b = 0, e = 0, cnt = 0;
+            if (i < tail) {
+                op.range(Q[i], b, e);
+                cnt = Op::count(b, e);
+                if (Op::kCountEdges) wedges += (unsigned long long)(e - b);
+            }
+            const bool hub = cnt > BIG;
+            const uint32_t hm = __ballot_sync(IMIN_FULL, hub);
+            if (hm) {
+                int hb = 0;
+                if (lane == 0) hb = atomicAdd(&sh.nbig[p], __popc(hm));
+                hb = __shfl_sync(IMIN_FULL, hb, 0);
+                const int my = hb + __popc(hm & lt_mask);
+                if (hub && my < BIGCAP) {
+                    sh.bb[my] = b;
+                    sh.be[my] = e;
+                    cnt = 0;
+                }
+            }
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(IMIN_FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const int total = __shfl_sync(IMIN_FULL, incl, 31);
+            const int excl = incl - cnt;
+            for (int t0 = 0; t0 < total; t0 += 32) {
+                const int t = t0 + lane;
+                // owner lane: the number of lanes whose running count is <= t
+                int pos = 0;
+#pragma unroll
+                for (int s = 16; s >= 1; s >>= 1) {
+                    const int c = __shfl_sync(IMIN_FULL, incl, pos + s - 1);
+                    if (c <= t) pos += s;
+                }
+                const int ob = __shfl_sync(IMIN_FULL, b, pos);
+                const int oe = __shfl_sync(IMIN_FULL, e, pos);
+                const int ox = __shfl_sync(IMIN_FULL, excl, pos);
+                pass(op, t < total, Op::first(ob) + (t - ox), ob, oe, K, bm, Q, cand, &sh.app[p], tail,
+                     lane, lt_mask);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) sh.app[p ^ 1] = 0;
+        // ---- phase 2: hubs, in pieces of PIECE items ----
+        const int nb = min(sh.nbig[p], BIGCAP);
+        if (nb > 0) {
+            if (warp == 0) {
+                int carry = 0;
+                for (int c0 = 0; c0 < nb; c0 += 32) {
+                    const int i = c0 + lane;
+                    int np = 0;
+                    if (i < nb) np = (Op::count(sh.bb[i], sh.be[i]) + PIECE - 1) / PIECE;
+                    int incl = np;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(IMIN_FULL, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    if (i < nb) sh.pp[i + 1] = carry + incl;
+                    carry += __shfl_sync(IMIN_FULL, incl, 31);
+                }
+                if (lane == 0) sh.pp[0] = 0;
+            }
+            __syncthreads();
+            const int npieces = sh.pp[nb];
+            for (;;) {
+                int pc = 0;
+                if (lane == 0) pc = atomicAdd(&sh.piece[p], 1);
+                pc = __shfl_sync(IMIN_FULL, pc, 0);
+                if (pc >= npieces) break;
+                int lo = 0, hi = nb;   // pp[lo] <= pc < pp[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (sh.pp[mid] <= pc) lo = mid; else hi = mid;
+                }
+                const int ob = sh.bb[lo], oe = sh.be[lo];
+                const int i0 = Op::first(ob) + (pc - sh.pp[lo]) * PIECE;
+                const int iend = min(i0 + PIECE, Op::first(ob) + Op::count(ob, oe));
+                for (int is = i0; is < iend; is += 32)
+                    pass(op, is + lane < iend, is + lane, ob, oe, K, bm, Q, cand, &sh.app[p], tail, lane,
+                         lt_mask);
+            }
+        }
+        __syncthreads();
+        const int ntail = tail + sh.app[p];
+        head = tail;
+        tail = ntail;
+        ++lvl;
+    }
+    return tail;
+}
+
+// bump allocation that never overshoots `cap`; returns ~0ull on failure
+__device__ __forceinline__ unsigned long long reserve_store(unsigned long long *cursor,
+                                                            unsigned long long cnt,
+                                                            unsigned long long cap)
+{
+    unsigned long long old = *(volatile unsigned long long *)cursor;
+    for (int tries = 0; tries < (1 << 20); ++tries) {
+        if (old + cnt > cap) return ~0ull;
+        const unsigned long long prev = atomicCAS(cursor, old, old + cnt);
+        if (prev == old) return old;
+        old = prev;
+    }
+    return ~0ull;
+}
+
+template <int BD, int MINB, bool SMEM_BM, bool STOP, bool UPPER>
+__global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
 {
     extern __shared__ uint32_t s_bm[];   // n bits when SMEM_BM
     __shared__ Shared<BD> sh;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    const int tid = threadIdx.x, lane = tid & 31;
     char *slot = a.slot_base + (size_t)blockIdx.x * a.slot_bytes;
-    World W;
-    W.bm = SMEM_BM ? s_bm : reinterpret_cast<uint32_t *>(slot);
-    W.Q = reinterpret_cast<int32_t *>(slot + a.off_queue);
-    int *const cand = sh.cand[warp];
+    uint32_t *const bm = SMEM_BM ? s_bm : reinterpret_cast<uint32_t *>(slot);
+    int32_t *const Q = reinterpret_cast<int32_t *>(slot + a.off_queue);
+    uint32_t *const bm2 = UPPER ? reinterpret_cast<uint32_t *>(slot + a.off_bm2) : nullptr;
+    int32_t *const Q2 = UPPER ? reinterpret_cast<int32_t *>(slot + a.off_q2) : nullptr;
+    const bool store = (a.flags & WF_STORE) != 0;
     if (SMEM_BM) {
         for (size_t w = tid; w < a.bm_words; w += BD) s_bm[w] = 0;
     }
@@ -171,7 +358,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_reach_kernel(const CArgs a)
             sh.rel = rel;
             sh.edges = 0;
             sh.slice[0] = sh.nbig[0] = sh.piece[0] = sh.app[0] = 0;
-            sh.app[1] = 0;
+            sh.slice[1] = sh.nbig[1] = sh.piece[1] = sh.app[1] = 0;
         }
         __syncthreads();
         const int got = sh.task;
@@ -179,156 +366,117 @@ __global__ void __launch_bounds__(BD, MINB) cta_reach_kernel(const CArgs a)
         ti = got;
         const uint32_t rel = sh.rel;
         const WTask &T = a.tasks[ti];
-        const int32_t *const row_ptr = T.row_ptr;
-        W.ce = T.ce;
-        W.klo = (uint32_t)T.q.key;
-        W.khi = (uint32_t)(T.q.key >> 32);
-        W.tag = T.q.tag;
-        W.inst = T.q.inst;
+        Coins K;
+        K.klo = (uint32_t)T.q.key;
+        K.khi = (uint32_t)(T.q.key >> 32);
+        K.tag = T.q.tag;
+        K.inst = T.q.inst;
         const uint32_t wrel = T.list ? (T.list[rel] & 0x7fffffffu) : rel;
-        W.j = (uint32_t)(T.first + (uint64_t)wrel);
+        K.j = (uint32_t)(T.first + (uint64_t)wrel);
         const int nS = T.q.nS;
 
         // ---- seeds, blocked nodes pre-marked as visited ----
         for (int i = tid; i < T.q.nB; i += BD) {
             const int v = T.q.B[i];
-            atomicOr(&W.bm[v >> 5], 1u << (v & 31));
+            atomicOr(&bm[v >> 5], 1u << (v & 31));
         }
         for (int i = tid; i < nS; i += BD) {
             const int s = T.q.S[i];
-            atomicOr(&W.bm[s >> 5], 1u << (s & 31));
-            W.Q[i] = s;
+            atomicOr(&bm[s >> 5], 1u << (s & 31));
+            Q[i] = s;
         }
         __syncthreads();
-        int head = 0, tail = nS, lvl = 0;
         unsigned long long wedges = 0;
-        while (head < tail) {
-            const int p = lvl & 1;
-            if (tid == 0) sh.slice[p ^ 1] = sh.nbig[p ^ 1] = sh.piece[p ^ 1] = 0;
-            // ---- phase 1: 32-node slices, one warp each ----
-            for (;;) {
-                int sl = 0;
-                if (lane == 0) sl = atomicAdd(&sh.slice[p], 1);
-                sl = __shfl_sync(IMIN_FULL, sl, 0);
-                const int base = head + sl * 32;
-                if (base >= tail) break;
-                const int i = base + lane;
-                int b = 0, e = 0, cnt = 0;
-                if (i < tail) {
-                    const int u = W.Q[i];
-                    b = row_ptr[u];
-                    e = row_ptr[u + 1];
-                    wedges += (unsigned long long)(e - b);
-                    if (e > b) cnt = ((e + 3) >> 2) - (b >> 2);
+        const Fwd fwd{T.row_ptr, T.ce};
+        const int tail = bfs<BD>(fwd, K, bm, Q, nS, sh, wedges);
+
+        // ---- upper bound: target from V'_s, reverse BFS inside the reached set ----
+        int tail2 = 0;
+        bool defer = false;
+        if (UPPER) {
+            if (tid == 0) {
+                int tn = -1;
+                if (T.q.nVs > 0) {
+                    const uint4 w = philox10_w(make_uint4(0xFFFFFFFFu, K.j, K.tag, K.inst), K.klo, K.khi);
+                    const unsigned long long r64 = ((unsigned long long)w.y << 32) | w.x;
+                    const unsigned long long idx = __umul64hi(r64, (unsigned long long)T.q.nVs);
+                    const int t = T.q.Vs[idx];
+                    const uint32_t fw = SMEM_BM ? bm[t >> 5] : __ldcg(bm + (t >> 5));
+                    const bool blk = T.q.blocked_bm && ((T.q.blocked_bm[t >> 5] >> (t & 31)) & 1u);
+                    if (((fw >> (t & 31)) & 1u) && !blk) tn = t;
                 }
-                const bool hub = cnt > BIG_GROUPS;
-                const uint32_t hm = __ballot_sync(IMIN_FULL, hub);
-                if (hm) {
-                    int hb = 0;
-                    if (lane == 0) hb = atomicAdd(&sh.nbig[p], __popc(hm));
-                    hb = __shfl_sync(IMIN_FULL, hb, 0);
-                    const int my = hb + __popc(hm & lt_mask);
-                    if (hub && my < BIGCAP) {
-                        sh.bb[my] = b;
-                        sh.be[my] = e;
-                        cnt = 0;
-                    }
+                if (tn >= 0) {
+                    atomicOr(&bm2[tn >> 5], 1u << (tn & 31));
+                    Q2[0] = tn;
                 }
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(IMIN_FULL, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int total = __shfl_sync(IMIN_FULL, incl, 31);
-                const int excl = incl - cnt;
-                for (int t0 = 0; t0 < total; t0 += 32) {
-                    const int t = t0 + lane;
-                    // owner lane: the number of lanes whose running count is <= t
-                    int pos = 0;
-#pragma unroll
-                    for (int s = 16; s >= 1; s >>= 1) {
-                        const int c = __shfl_sync(IMIN_FULL, incl, pos + s - 1);
-                        if (c <= t) pos += s;
-                    }
-                    const int ob = __shfl_sync(IMIN_FULL, b, pos);
-                    const int oe = __shfl_sync(IMIN_FULL, e, pos);
-                    const int ox = __shfl_sync(IMIN_FULL, excl, pos);
-                    expand_groups<SMEM_BM>(t < total, (ob >> 2) + (t - ox), ob, oe, W, cand,
-                                           &sh.app[p], tail, lane, lt_mask);
-                }
+                sh.target = tn;
+                sh.slice[0] = sh.nbig[0] = sh.piece[0] = sh.app[0] = 0;
+                sh.slice[1] = sh.nbig[1] = sh.piece[1] = sh.app[1] = 0;
             }
             __syncthreads();
-            if (tid == 0) sh.app[p ^ 1] = 0;
-            // ---- phase 2: hubs, in pieces of PIECE groups ----
-            const int nb = min(sh.nbig[p], BIGCAP);
-            if (nb > 0) {
-                if (warp == 0) {
-                    int carry = 0;
-                    for (int c0 = 0; c0 < nb; c0 += 32) {
-                        const int i = c0 + lane;
-                        int np = 0;
-                        if (i < nb) {
-                            const int g = ((sh.be[i] + 3) >> 2) - (sh.bb[i] >> 2);
-                            np = (g + PIECE - 1) / PIECE;
-                        }
-                        int incl = np;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const int y = __shfl_up_sync(IMIN_FULL, incl, o);
-                            if (lane >= o) incl += y;
-                        }
-                        if (i < nb) sh.pp[i + 1] = carry + incl;
-                        carry += __shfl_sync(IMIN_FULL, incl, 31);
-                    }
-                    if (lane == 0) sh.pp[0] = 0;
-                }
+            if (sh.target >= 0) {
+                const Rev<SMEM_BM> rev{T.in_ptr, T.in_src, T.in_eid, T.in_thr, bm, T.q.seed_bm,
+                                       T.q.blocked_bm};
+                tail2 = bfs<BD>(rev, K, bm2, Q2, 1, sh, wedges);
+            }
+            if (store) {
+                if (tid == 0)
+                    sh.sbase = tail2 > 0 ? reserve_store(T.out.set_cursor, (unsigned long long)tail2,
+                                                         T.out.set_cap)
+                                         : 0ull;
                 __syncthreads();
-                const int npieces = sh.pp[nb];
-                for (;;) {
-                    int pc = 0;
-                    if (lane == 0) pc = atomicAdd(&sh.piece[p], 1);
-                    pc = __shfl_sync(IMIN_FULL, pc, 0);
-                    if (pc >= npieces) break;
-                    int lo = 0, hi = nb;   // pp[lo] <= pc < pp[hi]
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sh.pp[mid] <= pc) lo = mid; else hi = mid;
+                defer = sh.sbase == ~0ull;
+            }
+        }
+
+        if (defer) {
+            // no store room: the world contributes nothing and is re-run after the host
+            // grows the store
+            if (tid == 0) {
+                const uint32_t d = atomicAdd(T.out.n_deferred, 1u);
+                if (d < T.out.deferred_cap)
+                    T.out.deferred[d] = wrel;
+                else
+                    atomicOr(T.out.err, DERR_INTERNAL);
+            }
+        } else {
+            // ---- outputs ----
+            if (T.out.reach)
+                for (int i = tid; i < tail; i += BD) atomicAdd(T.out.reach + Q[i], 1ull);
+            if (UPPER) {
+                if (T.out.credit_U)
+                    for (int i = tid; i < tail2; i += BD) atomicAdd(T.out.credit_U + Q2[i], 1ull);
+                if (store) {
+                    const unsigned long long sb = sh.sbase;
+                    for (int i = tid; i < tail2; i += BD) T.out.set_elem[sb + i] = Q2[i];
+                    if (tid == 0) {
+                        T.out.set_off[wrel] = sb;
+                        T.out.set_len[wrel] = (uint32_t)tail2;
                     }
-                    const int ob = sh.bb[lo], oe = sh.be[lo];
-                    const int g0 = (ob >> 2) + (pc - sh.pp[lo]) * PIECE;
-                    const int gend = min(g0 + PIECE, (oe + 3) >> 2);
-                    for (int gs = g0; gs < gend; gs += 32)
-                        expand_groups<SMEM_BM>(gs + lane < gend, gs + lane, ob, oe, W, cand, &sh.app[p],
-                                               tail, lane, lt_mask);
                 }
             }
-            __syncthreads();
-            const int ntail = tail + sh.app[p];
-            head = tail;
-            tail = ntail;
-            ++lvl;
-        }
-        // ---- outputs ----
-        if (T.out.reach)
-            for (int i = tid; i < tail; i += BD) atomicAdd(T.out.reach + W.Q[i], 1ull);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wedges += __shfl_xor_sync(IMIN_FULL, wedges, o);
-        if (lane == 0 && wedges) atomicAdd(&sh.edges, wedges);
-        __syncthreads();
-        if (tid == 0) {
-            atomicAdd(T.out.acc + 0, (unsigned long long)tail);
-            atomicAdd(T.out.acc + 1, sh.edges);
-            if (STOP) atomicAdd(T.out.acc + 3, (unsigned long long)tail);
-            atomicAdd(T.out.acc + 4, 1ull);
-            if (T.out.world_spread) T.out.world_spread[wrel] = (uint32_t)tail;
+            for (int o = 16; o > 0; o >>= 1) wedges += __shfl_xor_sync(IMIN_FULL, wedges, o);
+            if (lane == 0 && wedges) atomicAdd(&sh.edges, wedges);
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd(T.out.acc + 0, (unsigned long long)tail);
+                atomicAdd(T.out.acc + 1, sh.edges);
+                if (UPPER && tail2 > 0) atomicAdd(T.out.acc + 2, 1ull);
+                if (STOP) atomicAdd(T.out.acc + 3, (unsigned long long)tail);
+                atomicAdd(T.out.acc + 4, 1ull);
+                if (T.out.world_spread) T.out.world_spread[wrel] = (uint32_t)tail;
+            }
         }
         // ---- clear the visited marks ----
+        if (UPPER)
+            for (int i = tid; i < tail2; i += BD) bm2[Q2[i] >> 5] = 0;
         if (SMEM_BM) {
+            __syncthreads();
             for (size_t w = tid; w < a.bm_words; w += BD) s_bm[w] = 0;
         } else {
-            for (int i = tid; i < tail; i += BD) W.bm[W.Q[i] >> 5] = 0;
-            for (int i = tid; i < T.q.nB; i += BD) W.bm[T.q.B[i] >> 5] = 0;
+            for (int i = tid; i < tail; i += BD) bm[Q[i] >> 5] = 0;
+            for (int i = tid; i < T.q.nB; i += BD) bm[T.q.B[i] >> 5] = 0;
         }
         __syncthreads();
     }
@@ -336,43 +484,49 @@ __global__ void __launch_bounds__(BD, MINB) cta_reach_kernel(const CArgs a)
 
 inline size_t static_smem(int bd)
 {
-    return (size_t)(3 * BIGCAP + 1 + (bd / 32) * CAND + 8 + 2) * 4 + 8 + 16;
+    return (size_t)(3 * BIGCAP + 1 + (bd / 32) * CAND + 8 + 3) * 4 + 16 + 16;
 }
 
-template <int BD, int MINB, bool SMEM, bool STOP>
+template <int BD, int MINB, bool SMEM, bool STOP, bool UPPER>
 void launch_one(cudaStream_t st, const CArgs &a, int blocks, size_t smem)
 {
-    auto kern = cta_reach_kernel<BD, MINB, SMEM, STOP>;
+    auto kern = cta_world_kernel<BD, MINB, SMEM, STOP, UPPER>;
     if (smem > 48 * 1024)
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<blocks, BD, smem, st>>>(a);
     IM_CHECK_LAUNCH();
 }
 
+// kind: 0 reach-only, 1 reach-only with the stopping rule, 2 upper bound
 template <int BD, int MINB>
-void launch(cudaStream_t st, const CArgs &a, int blocks, bool smem_bm, bool stop, size_t smem)
+void launch(cudaStream_t st, const CArgs &a, int blocks, bool smem_bm, int kind, size_t smem)
 {
     if (smem_bm) {
-        if (stop) launch_one<BD, MINB, true, true>(st, a, blocks, smem);
-        else launch_one<BD, MINB, true, false>(st, a, blocks, smem);
+        if (kind == 2) launch_one<BD, MINB, true, false, true>(st, a, blocks, smem);
+        else if (kind == 1) launch_one<BD, MINB, true, true, false>(st, a, blocks, smem);
+        else launch_one<BD, MINB, true, false, false>(st, a, blocks, smem);
     } else {
-        if (stop) launch_one<BD, MINB, false, true>(st, a, blocks, smem);
-        else launch_one<BD, MINB, false, false>(st, a, blocks, smem);
+        if (kind == 2) launch_one<BD, MINB, false, false, true>(st, a, blocks, smem);
+        else if (kind == 1) launch_one<BD, MINB, false, true, false>(st, a, blocks, smem);
+        else launch_one<BD, MINB, false, false, false>(st, a, blocks, smem);
     }
 }
 
 // resident CTAs per SM (0 if the configuration cannot launch)
 template <int BD, int MINB>
-int occupancy(bool smem_bm, size_t smem)
+int occupancy(bool smem_bm, bool upper, size_t smem)
 {
     int nb = 0;
     cudaError_t e;
     if (smem_bm) {
-        auto kern = cta_reach_kernel<BD, MINB, true, true>;
+        auto kern = upper ? cta_world_kernel<BD, MINB, true, false, true>
+                          : cta_world_kernel<BD, MINB, true, true, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BD, smem);
     } else {
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cta_reach_kernel<BD, MINB, false, true>, BD, 0);
+        auto kern = upper ? cta_world_kernel<BD, MINB, false, false, true>
+                          : cta_world_kernel<BD, MINB, false, true, false>;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BD, 0);
     }
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -383,11 +537,11 @@ int occupancy(bool smem_bm, size_t smem)
 
 // explicit instantiations live in reach_cta_<BD>.cu
 #define IMIN_REACH_CTA_INSTANTIATE(BD_, MINB_)                                                          \
-    template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, bool, size_t);            \
-    template int occupancy<BD_, MINB_>(bool, size_t);
+    template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, int, size_t);             \
+    template int occupancy<BD_, MINB_>(bool, bool, size_t);
 
 #define IMIN_REACH_CTA_EXTERN(BD_, MINB_)                                                               \
-    extern template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, bool, size_t);     \
-    extern template int occupancy<BD_, MINB_>(bool, size_t);
+    extern template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, int, size_t);      \
+    extern template int occupancy<BD_, MINB_>(bool, bool, size_t);
 
 }  // namespace reach_cta

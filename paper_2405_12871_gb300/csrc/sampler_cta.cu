@@ -1,5 +1,5 @@
-// sampler_cta.cu -- host side of the CTA-per-world reach kernel (reach_cta.cuh):
-// slot layout, occupancy and the dispatch over CTA size and CTAs per SM.
+// sampler_cta.cu -- host side of the CTA-per-world kernel (reach_cta.cuh): slot
+// layout, occupancy and the dispatch over CTA size and CTAs per SM.
 #include "reach_cta.cuh"
 
 namespace reach_cta {
@@ -20,18 +20,24 @@ const int kNumCtaShapes = 6;
 
 size_t cta_static_smem(int bd) { return reach_cta::static_smem(bd); }
 
+// slot: [visited bitmap unless in shared memory] [queue]; upper-bound worlds add the
+// reverse pass's bitmap and queue
 size_t cta_slot_bytes(const SlotCfg &cfg)
 {
-    return (cfg.smem_bm ? 0 : al16(cfg.bm_words * 4)) + al16((size_t)cfg.qcap * 4);
+    size_t b = (cfg.smem_bm ? 0 : al16(cfg.bm_words * 4)) + al16((size_t)cfg.qcap * 4);
+    if (cfg.upper) b += al16(cfg.bm_words * 4) + al16((size_t)cfg.qcap * 4);
+    return b;
 }
 
-int cta_blocks_per_sm(int bd, int minb, bool smem_bm, size_t bm_words)
+int cta_blocks_per_sm(int bd, int minb, bool smem_bm, bool upper, size_t bm_words)
 {
     const size_t smem = smem_bm ? bm_words * 4 : 0;
     using namespace reach_cta;
-    if (bd == 256) return minb == 4 ? occupancy<256, 4>(smem_bm, smem) : occupancy<256, 8>(smem_bm, smem);
-    if (bd == 512) return minb == 2 ? occupancy<512, 2>(smem_bm, smem) : occupancy<512, 4>(smem_bm, smem);
-    return minb == 1 ? occupancy<1024, 1>(smem_bm, smem) : occupancy<1024, 2>(smem_bm, smem);
+    if (bd == 256)
+        return minb == 4 ? occupancy<256, 4>(smem_bm, upper, smem) : occupancy<256, 8>(smem_bm, upper, smem);
+    if (bd == 512)
+        return minb == 2 ? occupancy<512, 2>(smem_bm, upper, smem) : occupancy<512, 4>(smem_bm, upper, smem);
+    return minb == 1 ? occupancy<1024, 1>(smem_bm, upper, smem) : occupancy<1024, 2>(smem_bm, upper, smem);
 }
 
 void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t flags,
@@ -46,19 +52,22 @@ void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t 
     a.slot_bytes = cta_slot_bytes(cfg);
     a.bm_words = cfg.bm_words;
     a.off_queue = cfg.smem_bm ? 0 : al16(cfg.bm_words * 4);
-    const bool stop = (flags & WF_STOP) != 0;
+    a.off_bm2 = a.off_queue + al16((size_t)cfg.qcap * 4);
+    a.off_q2 = a.off_bm2 + al16(cfg.bm_words * 4);
+    a.flags = flags;
+    const int kind = (flags & WF_UPPER) ? 2 : ((flags & WF_STOP) ? 1 : 0);
     const size_t smem = cfg.smem_bm ? cfg.bm_words * 4 : 0;
     const int bd = cfg.cta_threads, mb = cfg.cta_minb;
     cudaStream_t st = ctx->stream;
     using namespace reach_cta;
     if (bd == 256) {
-        if (mb == 8) launch<256, 8>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
-        else launch<256, 4>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
+        if (mb == 8) launch<256, 8>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
+        else launch<256, 4>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
     } else if (bd == 512) {
-        if (mb == 4) launch<512, 4>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
-        else launch<512, 2>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
+        if (mb == 4) launch<512, 4>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
+        else launch<512, 2>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
     } else {
-        if (mb == 2) launch<1024, 2>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
-        else launch<1024, 1>(st, a, cfg.ctas, cfg.smem_bm, stop, smem);
+        if (mb == 2) launch<1024, 2>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
+        else launch<1024, 1>(st, a, cfg.ctas, cfg.smem_bm, kind, smem);
     }
 }

@@ -105,8 +105,9 @@ def hubs30k():
     rng = np.random.default_rng(13)
     B = rng.choice(np.setdiff1d(np.arange(g.n), S), 40, replace=False)
     og = oracle.OracleGraph.from_graph(g)
-    cases = (([], 700, 0), (B, 500, 77_777))
-    want = [og.sample(S, b, theta=t, key=3, tag=5, first=f, mode=1, per_world=True) for b, t, f in cases]
+    cases = (([], 700, 0, 1), (B, 500, 77_777, 1), ([], 600, 5, 5), (B, 400, 999, 4))
+    want = [og.sample(S, b, theta=t, key=3, tag=5, first=f, mode=md, per_world=True)
+            for b, t, f, md in cases]
     return g, S, cases, want
 
 
@@ -116,13 +117,14 @@ REACH_CONFIGS = ["warp"] + [f"{bd}x{mb}/{w}" for bd, mb in ((256, 4), (256, 8), 
 
 @pytest.mark.parametrize("cfg", REACH_CONFIGS)
 def test_reach_launch_configurations(ctx, monkeypatch, hubs30k, cfg):
-    """Reach-only worlds give the same bits under every launch configuration the
-    autotuner may pick: warp-per-world, or a CTA per world of 256/512/1024 threads
-    compiled for a given number of CTAs per SM, with the visited bitmap in global (g)
-    or shared (s) memory."""
+    """Reach-only and upper-bound (LRR) worlds give the same bits under every launch
+    configuration the autotuner may pick: warp-per-world, or a CTA per world of
+    256/512/1024 threads compiled for a given number of CTAs per SM, with the visited
+    bitmap in global (g) or shared (s) memory."""
     g, S, cases, want = hubs30k
     if cfg == "warp":
         monkeypatch.setenv("IMIN_REACH_CTA", "0")
+        monkeypatch.setenv("IMIN_UPPER_CTA", "0")
     else:
         shape, where = cfg.split("/")
         bd, mb = shape.split("x")
@@ -130,9 +132,11 @@ def test_reach_launch_configurations(ctx, monkeypatch, hubs30k, cfg):
         monkeypatch.setenv("IMIN_REACH_MINB", mb)
         monkeypatch.setenv("IMIN_REACH_SMEM", "1" if where == "s" else "0")
     G = ctx.load_graph(g)
-    for (blocked, theta, first), w in zip(cases, want):
-        got = G.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=1, per_world=True)
+    for (blocked, theta, first, md), w in zip(cases, want):
+        got = G.sample(S, blocked, theta=theta, key=3, tag=5, first=first, mode=md, per_world=True)
         assert_sample_equal(got, w)
+        if md & 4:
+            assert w["nonempty_lrr"] > 0
     G.free()
 
 
@@ -157,10 +161,11 @@ def test_reach_many_hubs_in_one_level(ctx, monkeypatch, cfg):
     G = ctx.load_graph(g)
     og = oracle.OracleGraph.from_graph(g)
     S = np.arange(ns)
-    got = G.sample(S, theta=200, key=9, tag=2, mode=1, per_world=True)
-    want = og.sample(S, theta=200, key=9, tag=2, mode=1, per_world=True)
-    assert_sample_equal(got, want)
-    assert want["total_spread"] > 200 * (ns + nh)
+    for mode in (1, 4):
+        got = G.sample(S, theta=200, key=9, tag=2, mode=mode, per_world=True)
+        want = og.sample(S, theta=200, key=9, tag=2, mode=mode, per_world=True)
+        assert_sample_equal(got, want)
+        assert want["total_spread"] > 200 * (ns + nh)
     G.free()
 
 

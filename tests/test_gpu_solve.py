@@ -130,3 +130,18 @@ def test_autotuner_choice_is_cached_and_changes_nothing(ctx, monkeypatch):
     compare(off, first)
     for x in (G, H, K):
         x.free()
+
+
+def test_store_growth_path(ctx, monkeypatch):
+    """With CP and LRR stores reserved almost empty, most worlds are deferred for lack of
+    store room and re-run after the store grows; the results are unchanged."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
+    S = synth.seeds_top_outdeg(g, 10, 0.01, seed=4)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=20, eps=0.3, delta=1.0 / g.n, key=3)
+    monkeypatch.setenv("IMIN_STORE_TIGHT", "1")
+    G = ctx.load_graph(g)
+    got = G.solve(S, **kw)
+    G.free()
+    monkeypatch.delenv("IMIN_STORE_TIGHT")
+    compare(got, og.solve(S, **kw))
