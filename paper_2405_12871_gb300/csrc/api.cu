@@ -82,13 +82,13 @@ struct Query {
     std::vector<int32_t> S;       // sorted, distinct
     std::vector<int32_t> blocked; // sorted, distinct
     std::vector<uint8_t> is_seed, is_blocked;
-    DBuf dS, dseed_bm, dblk_bm, dB, dVs;
-    std::vector<int32_t> Vs;      // sorted ascending
+    DBuf dS, dseed_bm, dblk_bm, dB, dVs;   // dVs: V'_s sorted ascending (nVs entries)
+    int32_t nVs = 0;
     size_t words = 0;
     void release()
     {
         for (DBuf *b : {&dS, &dseed_bm, &dblk_bm, &dB, &dVs}) b->release();
-        std::vector<int32_t>().swap(Vs);
+        nVs = 0;
         std::vector<uint8_t>().swap(is_seed);
         std::vector<uint8_t>().swap(is_blocked);
     }
@@ -108,30 +108,6 @@ void check_nodes(const imin_graph *g, const int32_t *a, int32_t cnt, const char 
 }
 
 // V'_s: nodes reachable from S in G[V \ blocked] over edges with p > 0, minus S.
-void compute_Vs(const imin_graph *g, Query &q)
-{
-    const int32_t n = g->n;
-    std::vector<uint8_t> mark(n, 0);
-    std::vector<int32_t> queue;
-    queue.reserve(1024);
-    for (int32_t s : q.S) {
-        mark[s] = 1;
-        queue.push_back(s);
-    }
-    for (size_t h = 0; h < queue.size(); ++h) {
-        const int32_t u = queue[h];
-        for (int32_t e = g->h_row_ptr[u]; e < g->h_row_ptr[u + 1]; ++e) {
-            const int32_t v = g->h_col[e];
-            if (g->h_thr[e] == 0 || mark[v] || q.is_blocked[v]) continue;
-            mark[v] = 1;
-            queue.push_back(v);
-        }
-    }
-    q.Vs.clear();
-    for (int32_t v = 0; v < n; ++v)
-        if (mark[v] && !q.is_seed[v]) q.Vs.push_back(v);
-}
-
 void prepare_query(imin_ctx *ctx, const imin_graph *g, Query &q, const int32_t *S, int32_t nS,
                    const int32_t *B, int32_t nB, bool need_vs)
 {
@@ -159,12 +135,10 @@ void prepare_query(imin_ctx *ctx, const imin_graph *g, Query &q, const int32_t *
         fill_bitmap(ctx, q.dblk_bm.as<uint32_t>(), q.words, q.dB.as<int32_t>(),
                     (int32_t)q.blocked.size());
     }
-    if (need_vs) {
-        compute_Vs(g, q);
-        q.dVs.ensure(ctx, q.Vs.size() * 4 + 16);
-        if (!q.Vs.empty())
-            IM_CUDA(cudaMemcpyAsync(q.dVs.p, q.Vs.data(), q.Vs.size() * 4, cudaMemcpyHostToDevice, st));
-    }
+    q.nVs = 0;
+    if (need_vs)
+        q.nVs = device_reach_set(ctx, g, q.dS.as<int32_t>(), (int32_t)q.S.size(), q.dseed_bm.as<uint32_t>(),
+                                 q.blocked.empty() ? nullptr : q.dblk_bm.as<uint32_t>(), q.dVs);
     IM_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -177,8 +151,8 @@ QueryDev qdev(const Query &q, uint64_t key, uint32_t tag, uint32_t inst)
     d.blocked_bm = q.blocked.empty() ? nullptr : q.dblk_bm.as<uint32_t>();
     d.B = q.blocked.empty() ? nullptr : q.dB.as<int32_t>();
     d.nB = (int32_t)q.blocked.size();
-    d.Vs = q.Vs.empty() ? nullptr : q.dVs.as<int32_t>();
-    d.nVs = (int32_t)q.Vs.size();
+    d.Vs = q.nVs > 0 ? q.dVs.as<int32_t>() : nullptr;
+    d.nVs = q.nVs;
     d.key = key;
     d.tag = tag;
     d.inst = inst;
@@ -648,7 +622,7 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
     std::vector<DBuf> spread(ns);
     for (size_t i = 0; i < ns; ++i) {
         StopSpec &sp = specs[i];
-        W[i] = (double)sp.q->Vs.size() + (double)sp.q->S.size();
+        W[i] = (double)sp.q->nVs + (double)sp.q->S.size();
         const double ups = 4.0 * (IM_E - 2.0) * std::log(2.0 / sp.dprime) / (sp.beta * sp.beta);
         ups1[i] = 1.0 + (1.0 + sp.beta) * ups;
         const double Td = std::ceil(ups1[i] * W[i]);
@@ -1037,7 +1011,7 @@ void inst_prepare(imin_ctx *ctx, Inst &I, const int32_t *S_in, int32_t nS)
             if (g->h_thr[e] > 0 && !I.q.is_seed[g->h_col[e]]) inON[g->h_col[e]] = 1;
     for (int32_t v = 0; v < n; ++v)
         if (inON[v]) I.ON.push_back(v);
-    I.nVs = (int32_t)I.q.Vs.size();
+    I.nVs = I.q.nVs;
     if ((int32_t)I.ON.size() <= k) {   // Algorithm 4, lines 2-3; Sec. 5.3 (nothing sampled)
         put(I.blockers, I.ON);
         put(I.B_L, I.ON);
@@ -1378,6 +1352,7 @@ struct Scheduler {
             gjp.push_back(&gj[i]);
         }
         kms[3] += greedy_batch(ctx, gb, gjp);
+        const double t_greedy = tg.ms();
         for (size_t i = 0; i < bl.size(); ++i) {
             Inst &I = *bl[i];
             Bound &B = upper ? I.U : I.L;
@@ -1402,6 +1377,10 @@ struct Scheduler {
             }
         }
         ms[upper ? 4 : 2] += tg.ms();
+        if (const char *tr = std::getenv("IMIN_TRACE"))
+            if (tr[0] == '1')
+                std::fprintf(stderr, "[imin] %s bound step: %zu instance(s), greedy %.2f ms, coverage and check %.2f ms\n",
+                             upper ? "upper" : "lower", bl.size(), t_greedy, tg.ms() - t_greedy);
     }
 
     // one step; returns the instances finished in it

@@ -252,6 +252,12 @@ void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_gr
 // ---------------------------------------------------------------------------
 // Utilities (graph.cu)
 // ---------------------------------------------------------------------------
+// V'_s (vs.cu): nodes reachable from S over edges of nonzero probability, avoiding the
+// blocked nodes (blk_bm may be null), S excluded; written to `out` in ascending order.
+// Returns |V'_s|.
+int32_t device_reach_set(imin_ctx *ctx, const imin_graph *g, const int32_t *dS, int32_t nS,
+                         const uint32_t *seed_bm, const uint32_t *blk_bm, DBuf &out);
+
 // exclusive scan of n int64 values in place (d_tmp: >= scan_tmp_bytes(n) bytes)
 size_t scan_tmp_bytes(int64_t n);
 void exclusive_scan_i64(imin_ctx *ctx, long long *d, int64_t n, void *d_tmp);

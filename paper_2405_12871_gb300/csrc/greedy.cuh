@@ -15,7 +15,7 @@ struct GState {
     int32_t hi;                 // top-k radix select: bits >= hi are fixed
     int32_t krem;               // top-k radix select: values still to take
     int32_t tdone;              // top-k radix select finished
-    int32_t pad;
+    int32_t npass;              // top-k radix select: digit passes this round needs
 };
 
 struct CpStore;
@@ -24,6 +24,8 @@ struct LrrStore;
 // One Max-Coverage instance as the batched round kernels see it.
 struct GInst {
     int32_t n, k;
+    const int32_t *cand;     // nodes with a nonzero initial gain, ascending (ncand)
+    int32_t ncand;
     unsigned long long *gain;
     GState *st;
     int32_t *B;
@@ -32,12 +34,14 @@ struct GInst {
     unsigned long long *hsum;
     unsigned long long *part_g;
     int32_t *part_v;
-    unsigned int *done_ctr;
+    unsigned int *done_ctr;    // argmax blocks finished this round
+    unsigned int *done_ctr2;   // histogram blocks finished this pass (persistent kernel)
     int32_t blk0, nblk;      // blocks of the argmax / histogram grids
     int32_t ublk0, unblk;    // blocks of the decrement grid
     const long long *inv_off;
     // CP records
     const long long *inv_rec;
+    const long long *inv_cpre;   // running count of update chunks over inv_rec (R + 1)
     const int32_t *rnode, *rpar, *rsize;
     int32_t *contrib;
     uint8_t *covered;
@@ -65,7 +69,7 @@ struct GreedyJob {
 };
 
 struct GreedyBufs {
-    DBuf arena, ginst, blkmap;
+    DBuf arena, ginst, blkmap, cand, flags, scan_tmp, ncand;
 };
 
 // CP records of one collection (C1 or C2), in DT preorder per world.
@@ -75,10 +79,11 @@ struct CpStore {
     long long count = 0;           // records stored
     unsigned long long cap = 0;
     uint64_t worlds = 0;           // |C|
-    DBuf inv_off, inv_rec, fill, contrib, covered, scan_tmp;
+    DBuf inv_off, inv_rec, inv_cpre, fill, contrib, covered, scan_tmp;
     void release()
     {
-        for (DBuf *b : {&node, &par, &size, &cursor, &inv_off, &inv_rec, &fill, &contrib, &covered, &scan_tmp})
+        for (DBuf *b : {&node, &par, &size, &cursor, &inv_off, &inv_rec, &inv_cpre, &fill, &contrib, &covered,
+                        &scan_tmp})
             b->release();
         count = 0;
         cap = 0;

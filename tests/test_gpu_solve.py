@@ -54,7 +54,11 @@ def test_er1k_stopping_rules(ctx, eps, k):
     G.free()
 
 
-def test_small_chung_lu_solve(ctx):
+@pytest.mark.parametrize("persistent", ["1", "0"])
+def test_small_chung_lu_solve(ctx, monkeypatch, persistent):
+    """Both forms of the greedy rounds: one cooperative persistent launch, or one
+    launch per round step."""
+    monkeypatch.setenv("IMIN_GREEDY_PERSISTENT", persistent)
     g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
     S = synth.seeds_top_outdeg(g, 10, 0.01, seed=4)
     G = ctx.load_graph(g)
