@@ -239,7 +239,20 @@ struct Runner {
         const char *cta_env = std::getenv("IMIN_REACH_CTA");
         const char *upper_env = std::getenv("IMIN_UPPER_CTA");
         const bool upper_cta = c.upper && !(upper_env && upper_env[0] == '0');
-        if (!c.lower && (!c.upper || upper_cta) && !big) {
+        // lower-bound worlds (without the upper bound in the same pass) also run one per
+        // CTA (IMIN_LOWER_CTA=0: warp per world); their edge pairs get a fixed budget and
+        // a world that needs more is deferred to the large-slot pass
+        const char *lower_env = std::getenv("IMIN_LOWER_CTA");
+        const bool lower_cta = c.lower && !c.upper && !(lower_env && lower_env[0] == '0');
+        if ((lower_cta || (!c.lower && (!c.upper || upper_cta))) && !big) {
+            if (c.lower) {
+                c.ecap = (int32_t)std::min<int64_t>(std::max<int64_t>(m, 1),
+                                                    std::max<int64_t>(1 << 20, 2 * ((int64_t)n + 1)));
+                if (const char *env = std::getenv("IMIN_SLOT_QCAP")) {   // test hook, as below
+                    const long v = std::strtol(env, nullptr, 10);
+                    if (v > 0 && v < c.ecap) c.ecap = (int32_t)v;
+                }
+            }
             if (force) {   // autotuner probe
                 SlotCfg f = *force;
                 f.upper = c.upper;
@@ -251,8 +264,20 @@ struct Runner {
                 c.cta_threads = gref->tuned_bd;
                 c.cta_minb = gref->tuned_minb;
                 c.qcap = n + 1;
-                c.ecap = 0;
                 c.ctas = gref->tuned_ctas;
+                if (c.lower || c.upper) {
+                    // the same shape, at most as many CTAs per SM as the bound's kernel fits
+                    if (c.smem_bm) {
+                        int optin = 0;
+                        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+                        cudaGetLastError();
+                        if (c.bm_words * 4 + cta_static_smem(c.cta_threads, c.lower) + 1024 > (size_t)optin)
+                            c.smem_bm = false;
+                    }
+                    const int occ = cta_blocks_per_sm(c.cta_threads, c.cta_minb, c.smem_bm, c.upper, c.lower,
+                                                      c.bm_words);
+                    c.ctas = ctx->num_sms * std::max(1, std::min(gref->tuned_ctas / ctx->num_sms, occ));
+                }
                 c.warps = c.ctas * (c.cta_threads / 32);
                 return cap_ctas(c);
             }
@@ -274,14 +299,14 @@ struct Runner {
                     for (int i = 0; i < kNumCtaShapes; ++i)
                         if (kCtaShapes[i][0] == bd && kCtaShapes[i][1] == v) minb = (int)v;
                 }
-                c.smem_bm = c.bm_words * 4 + cta_static_smem(bd) + 1024 <= (size_t)optin;
+                c.smem_bm = c.bm_words * 4 + cta_static_smem(bd, c.lower) + 1024 <= (size_t)optin;
                 if (const char *env = std::getenv("IMIN_REACH_SMEM"))
                     if (env[0] == '0') c.smem_bm = false;
                 c.cta_threads = bd;
                 c.cta_minb = minb;
                 c.qcap = n + 1;
-                c.ecap = 0;
-                c.ctas = ctx->num_sms * std::max(1, cta_blocks_per_sm(bd, minb, c.smem_bm, c.upper, c.bm_words));
+                c.ctas = ctx->num_sms *
+                         std::max(1, cta_blocks_per_sm(bd, minb, c.smem_bm, c.upper, c.lower, c.bm_words));
                 c.warps = c.ctas * (bd / 32);
                 return cap_ctas(c);
             }
@@ -516,7 +541,7 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
             const int bd = kCtaShapes[i][0], minb = kCtaShapes[i][1];
             const bool smem = sm == 1;
             if (smem && words * 4 + cta_static_smem(bd) + 1024 > (size_t)optin) continue;
-            const int nb = std::min(minb, cta_blocks_per_sm(bd, minb, smem, false, words));
+            const int nb = std::min(minb, cta_blocks_per_sm(bd, minb, smem, false, false, words));
             if (nb <= 0) continue;
             // a shape compiled for more CTAs per SM than fit is the same launch as a
             // smaller one with fewer registers: skip it

@@ -237,9 +237,9 @@ WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t
 // {threads per CTA, CTAs per SM}
 extern const int kCtaShapes[][2];
 extern const int kNumCtaShapes;
-size_t cta_static_smem(int bd);
+size_t cta_static_smem(int bd, bool lower = false);
 size_t cta_slot_bytes(const SlotCfg &cfg);
-int cta_blocks_per_sm(int bd, int minb, bool smem_bm, bool upper, size_t bm_words);
+int cta_blocks_per_sm(int bd, int minb, bool smem_bm, bool upper, bool lower, size_t bm_words);
 void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t flags,
                       const SlotCfg &cfg, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
 

@@ -37,6 +37,10 @@ struct CArgs {
     size_t slot_bytes;
     size_t bm_words;
     size_t off_queue, off_bm2, off_q2;
+    // lower bound: node -> queue position, per position BFS level, dominator
+    // estimate, subtree size, preorder rank, child cursor; level starts; edge pairs
+    size_t off_loc, off_lvl, off_idom, off_sz, off_pre, off_cur, off_lstart, off_pu, off_pv;
+    int ecap;
     uint32_t flags;
 };
 
@@ -45,17 +49,70 @@ constexpr int PIECE = 128;    // items per phase-2 claim
 constexpr int BIGCAP = 256;   // hubs staged per level (further hubs stay in phase 1)
 constexpr int CAND = 128;     // per-warp staging: 32 lanes x 4 edges
 
-template <int BD>
+template <int BD, bool SRC = false>
 struct Shared {
     int pp[BIGCAP + 1];   // running piece counts of the staged hubs
-    int bb[BIGCAP], be[BIGCAP];
+    int bb[BIGCAP], be[BIGCAP], bi[BIGCAP];   // hub edge range and queue position
     int cand[BD / 32][CAND];
+    int cand2[SRC ? BD / 32 : 1][SRC ? CAND : 1];   // queue position of each candidate's source
     int slice[2], nbig[2], piece[2], app[2];   // per level parity
     int task;
     uint32_t rel;
     int target;
+    int npairs;           // lower bound: live edges recorded
+    int root;             // lower bound: preorder ranges handed to dominator-tree roots
+    int nlev;
     unsigned long long edges;
     unsigned long long sbase;
+};
+
+// What a traversal records besides the queue.  NoRec: nothing (reach-only and the
+// upper bound).  DomRec (lower bound): for each new node its queue position (loc), BFS
+// level and BFS parent (the first estimate of its immediate dominator), and every live
+// edge into a non-seed node as a (source position, target) pair.
+struct NoRec {
+    static constexpr bool kOn = false;
+    __device__ __forceinline__ uint32_t filter(uint32_t live, const int4 &) const { return live; }
+    __device__ __forceinline__ void on_new(int, int, int, int) const {}
+    __device__ __forceinline__ bool want_pair(int) const { return false; }
+    __device__ __forceinline__ void put_pair(int, int, int) const {}
+    __device__ __forceinline__ void level_start(int, int) const {}
+};
+
+struct DomRec {
+    static constexpr bool kOn = true;
+    int32_t *loc, *lvl, *idom, *pu, *pv, *lstart;
+    const uint32_t *seed_bm, *blocked_bm;
+    int ecap;
+    __device__ __forceinline__ static bool bit(const uint32_t *bm, int v)
+    {
+        return (__ldg(bm + (v >> 5)) >> (v & 31)) & 1u;
+    }
+    // blocked nodes are never entered: their in-edges are neither followed nor recorded
+    __device__ __forceinline__ uint32_t filter(uint32_t live, const int4 &c4) const
+    {
+        if (!blocked_bm || !live) return live;
+        if ((live & 1u) && bit(blocked_bm, c4.x)) live &= ~1u;
+        if ((live & 2u) && bit(blocked_bm, c4.y)) live &= ~2u;
+        if ((live & 4u) && bit(blocked_bm, c4.z)) live &= ~4u;
+        if ((live & 8u) && bit(blocked_bm, c4.w)) live &= ~8u;
+        return live;
+    }
+    __device__ __forceinline__ void on_new(int v, int pos, int src, int level) const
+    {
+        loc[v] = pos;
+        lvl[pos] = level;
+        idom[pos] = src;
+    }
+    __device__ __forceinline__ bool want_pair(int v) const { return !bit(seed_bm, v); }
+    __device__ __forceinline__ void put_pair(int idx, int src, int v) const
+    {
+        if (idx < ecap) {
+            pu[idx] = src;
+            pv[idx] = v;
+        }
+    }
+    __device__ __forceinline__ void level_start(int level, int head) const { lstart[level] = head; }
 };
 
 __device__ __forceinline__ uint4 philox10_w(uint4 c, uint32_t k0, uint32_t k1)
@@ -140,14 +197,14 @@ struct Rev {
 
 // One pass over one item per lane (act): stage the live targets of the warp, claim
 // them in bm and append the new ones to Q[tail + ...].  All 32 lanes must call it.
-template <class Op>
-__device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int oe, const Coins &K,
-                                     uint32_t *bm, int32_t *Q, int *cand, int *app, int tail, int lane,
-                                     uint32_t lt_mask)
+template <class Op, class Rec>
+__device__ __forceinline__ void pass(const Op &op, const Rec &rec, bool act, int it, int ob, int oe, int src,
+                                     int level, const Coins &K, uint32_t *bm, int32_t *Q, int *cand,
+                                     int *cand2, int *app, int *npairs, int tail, int lane, uint32_t lt_mask)
 {
     uint32_t live = 0;
     int4 c4 = make_int4(0, 0, 0, 0);
-    if (act) live = op.live(it, ob, oe, K, c4);
+    if (act) live = rec.filter(op.live(it, ob, oe, K, c4), c4);
     const int nl = __popc(live);
     int incl = nl;
 #pragma unroll
@@ -158,6 +215,8 @@ __device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int
     const int tot = __shfl_sync(IMIN_FULL, incl, 31);
     if (tot == 0) return;
     int off = incl - nl;
+    if (Rec::kOn)
+        for (int c = 0; c < nl; ++c) cand2[off + c] = src;
     if (live & 1u) cand[off++] = c4.x;
     if (live & 2u) cand[off++] = c4.y;
     if (live & 4u) cand[off++] = c4.z;
@@ -165,10 +224,14 @@ __device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int
     __syncwarp();
     for (int k0 = 0; k0 < tot; k0 += 32) {
         const int k = k0 + lane;
-        bool fresh = false;
-        int v = 0;
+        bool fresh = false, pair = false;
+        int v = 0, sv = 0;
         if (k < tot) {
             v = cand[k];
+            if (Rec::kOn) {
+                sv = cand2[k];
+                pair = rec.want_pair(v);
+            }
             const uint32_t bit = 1u << (v & 31);
             const uint32_t old = atomicOr(&bm[v >> 5], bit);
             fresh = !(old & bit);
@@ -178,7 +241,20 @@ __device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int
             int base = 0;
             if (lane == 0) base = atomicAdd(app, __popc(bal));
             base = __shfl_sync(IMIN_FULL, base, 0);
-            if (fresh) Q[tail + base + __popc(bal & lt_mask)] = v;
+            if (fresh) {
+                const int pos = tail + base + __popc(bal & lt_mask);
+                Q[pos] = v;
+                rec.on_new(v, pos, sv, level + 1);
+            }
+        }
+        if (Rec::kOn) {
+            const uint32_t pb = __ballot_sync(IMIN_FULL, pair);
+            if (pb) {
+                int pbase = 0;
+                if (lane == 0) pbase = atomicAdd(npairs, __popc(pb));
+                pbase = __shfl_sync(IMIN_FULL, pbase, 0);
+                if (pair) rec.put_pair(pbase + __popc(pb & lt_mask), sv, v);
+            }
         }
     }
     __syncwarp();
@@ -187,17 +263,21 @@ __device__ __forceinline__ void pass(const Op &op, bool act, int it, int ob, int
 // Breadth-first expansion of Q[0, tail0) until no level adds a node; returns the
 // final tail.  The caller zeroes the counters of both parities and passes a CTA
 // barrier before the call; the call ends with a CTA barrier.
-template <int BD, class Op>
-__device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, int32_t *Q, int tail0,
-                                   Shared<BD> &sh, unsigned long long &wedges)
+template <int BD, bool SRC, class Op, class Rec>
+__device__ __forceinline__ int bfs(const Op &op, const Rec &rec, const Coins &K, uint32_t *bm, int32_t *Q,
+                                   int tail0, Shared<BD, SRC> &sh, unsigned long long &wedges)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
     int *const cand = sh.cand[warp];
+    int *const cand2 = sh.cand2[SRC ? warp : 0];
     int head = 0, tail = tail0, lvl = 0;
     while (head < tail) {
         const int p = lvl & 1;
-        if (tid == 0) sh.slice[p ^ 1] = sh.nbig[p ^ 1] = sh.piece[p ^ 1] = 0;
+        if (tid == 0) {
+            sh.slice[p ^ 1] = sh.nbig[p ^ 1] = sh.piece[p ^ 1] = 0;
+            rec.level_start(lvl, head);
+        }
         // ---- phase 1: 32-node slices, one warp each ----
         for (;;) {
             int sl = 0;
@@ -222,6 +302,7 @@ __device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, i
                 if (hub && my < BIGCAP) {
                     sh.bb[my] = b;
                     sh.be[my] = e;
+                    sh.bi[my] = i;
                     cnt = 0;
                 }
             }
@@ -245,8 +326,8 @@ __device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, i
                 const int ob = __shfl_sync(IMIN_FULL, b, pos);
                 const int oe = __shfl_sync(IMIN_FULL, e, pos);
                 const int ox = __shfl_sync(IMIN_FULL, excl, pos);
-                pass(op, t < total, Op::first(ob) + (t - ox), ob, oe, K, bm, Q, cand, &sh.app[p], tail,
-                     lane, lt_mask);
+                pass(op, rec, t < total, Op::first(ob) + (t - ox), ob, oe, base + pos, lvl, K, bm, Q, cand,
+                     cand2, &sh.app[p], &sh.npairs, tail, lane, lt_mask);
             }
         }
         __syncthreads();
@@ -283,12 +364,12 @@ __device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, i
                     const int mid = (lo + hi) >> 1;
                     if (sh.pp[mid] <= pc) lo = mid; else hi = mid;
                 }
-                const int ob = sh.bb[lo], oe = sh.be[lo];
+                const int ob = sh.bb[lo], oe = sh.be[lo], oi = sh.bi[lo];
                 const int i0 = Op::first(ob) + (pc - sh.pp[lo]) * PIECE;
                 const int iend = min(i0 + PIECE, Op::first(ob) + Op::count(ob, oe));
                 for (int is = i0; is < iend; is += 32)
-                    pass(op, is + lane < iend, is + lane, ob, oe, K, bm, Q, cand, &sh.app[p], tail, lane,
-                         lt_mask);
+                    pass(op, rec, is + lane < iend, is + lane, ob, oe, oi, lvl, K, bm, Q, cand, cand2, &sh.app[p],
+                         &sh.npairs, tail, lane, lt_mask);
             }
         }
         __syncthreads();
@@ -296,6 +377,10 @@ __device__ __forceinline__ int bfs(const Op &op, const Coins &K, uint32_t *bm, i
         head = tail;
         tail = ntail;
         ++lvl;
+    }
+    if (tid == 0) {
+        rec.level_start(lvl, tail);
+        sh.nlev = lvl;
     }
     return tail;
 }
@@ -388,7 +473,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
         __syncthreads();
         unsigned long long wedges = 0;
         const Fwd fwd{T.row_ptr, T.ce};
-        const int tail = bfs<BD>(fwd, K, bm, Q, nS, sh, wedges);
+        const int tail = bfs<BD, false>(fwd, NoRec{}, K, bm, Q, nS, sh, wedges);
 
         // ---- upper bound: target from V'_s, reverse BFS inside the reached set ----
         int tail2 = 0;
@@ -417,7 +502,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
             if (sh.target >= 0) {
                 const Rev<SMEM_BM> rev{T.in_ptr, T.in_src, T.in_eid, T.in_thr, bm, T.q.seed_bm,
                                        T.q.blocked_bm};
-                tail2 = bfs<BD>(rev, K, bm2, Q2, 1, sh, wedges);
+                tail2 = bfs<BD, false>(rev, NoRec{}, K, bm2, Q2, 1, sh, wedges);
             }
             if (store) {
                 if (tid == 0)
@@ -482,9 +567,229 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
     }
 }
 
-inline size_t static_smem(int bd)
+// LCA of queue positions a and b in the current dominator-estimate tree (-1 = the
+// virtual root s): the deeper one (by BFS level) steps to its estimate until they meet.
+__device__ __forceinline__ int dt_lca(int a, int b, const int32_t *lvl, const int32_t *idom, int nS)
 {
-    return (size_t)(3 * BIGCAP + 1 + (bd / 32) * CAND + 8 + 3) * 4 + 16 + 16;
+    for (int guard = 0; guard < (1 << 22) && a != b; ++guard) {
+        const int la = a < 0 ? -1 : lvl[a];
+        const int lb = b < 0 ? -1 : lvl[b];
+        if (la >= lb)
+            a = (a < nS) ? -1 : __ldcg(idom + a);
+        else
+            b = (b < nS) ? -1 : __ldcg(idom + b);
+    }
+    return a;
+}
+
+// Lower-bound worlds (Algorithm 2, Local Sampling; Sec. 4): one CTA per world.
+//   1. forward BFS recording positions, levels, BFS parents and live edge pairs;
+//   2. immediate dominators by repeated relaxation idom(v) <- LCA(idom(v), u) over the
+//      live edges (u, v) until a pass changes nothing (a dominator is an ancestor in
+//      every BFS tree, so the BFS parents are a valid first estimate);
+//   3. subtree sizes bottom-up by level, credit_L[v] += subtree size (the number of
+//      CP sets containing v);
+//   4. CP records in dominator-tree preorder: node, distance back to the parent record
+//      (0 for a root), subtree size.
+// A world whose edge pairs overflow the slot is deferred to a large slot (top bit),
+// one that finds no store room is deferred until the host grows the store.
+template <int BD, int MINB, bool SMEM_BM>
+__global__ void __launch_bounds__(BD, MINB) cta_lower_kernel(const CArgs a)
+{
+    extern __shared__ uint32_t s_bm[];
+    __shared__ Shared<BD, true> sh;
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    char *slot = a.slot_base + (size_t)blockIdx.x * a.slot_bytes;
+    uint32_t *const bm = SMEM_BM ? s_bm : reinterpret_cast<uint32_t *>(slot);
+    int32_t *const Q = reinterpret_cast<int32_t *>(slot + a.off_queue);
+    int32_t *const loc = reinterpret_cast<int32_t *>(slot + a.off_loc);
+    int32_t *const lvl = reinterpret_cast<int32_t *>(slot + a.off_lvl);
+    int32_t *const idom = reinterpret_cast<int32_t *>(slot + a.off_idom);
+    int32_t *const sz = reinterpret_cast<int32_t *>(slot + a.off_sz);
+    int32_t *const pre = reinterpret_cast<int32_t *>(slot + a.off_pre);
+    int32_t *const cur = reinterpret_cast<int32_t *>(slot + a.off_cur);
+    int32_t *const lstart = reinterpret_cast<int32_t *>(slot + a.off_lstart);
+    int32_t *const pu = reinterpret_cast<int32_t *>(slot + a.off_pu);
+    int32_t *const pv = reinterpret_cast<int32_t *>(slot + a.off_pv);
+    const bool store = (a.flags & WF_STORE) != 0;
+    if (SMEM_BM) {
+        for (size_t w = tid; w < a.bm_words; w += BD) s_bm[w] = 0;
+    }
+    int ti = (int)(blockIdx.x % (unsigned)a.ntasks);
+    for (;;) {
+        if (tid == 0) {
+            int got = -1;
+            uint32_t rel = 0;
+            for (int scan = 0; scan < a.ntasks; ++scan) {
+                const int t = (ti + scan) % a.ntasks;
+                if (*(volatile uint32_t *)(a.task_done + t)) continue;
+                const uint32_t r = atomicAdd(a.task_claim + t, 1u);
+                if (r >= a.tasks[t].count) {
+                    a.task_done[t] = 1u;
+                    continue;
+                }
+                got = t;
+                rel = r;
+                break;
+            }
+            sh.task = got;
+            sh.rel = rel;
+            sh.edges = 0;
+            sh.npairs = 0;
+            sh.root = 0;
+            sh.slice[0] = sh.nbig[0] = sh.piece[0] = sh.app[0] = 0;
+            sh.slice[1] = sh.nbig[1] = sh.piece[1] = sh.app[1] = 0;
+        }
+        __syncthreads();
+        const int got = sh.task;
+        if (got < 0) break;
+        ti = got;
+        const uint32_t rel = sh.rel;
+        const WTask &T = a.tasks[ti];
+        Coins K;
+        K.klo = (uint32_t)T.q.key;
+        K.khi = (uint32_t)(T.q.key >> 32);
+        K.tag = T.q.tag;
+        K.inst = T.q.inst;
+        const uint32_t wrel = T.list ? (T.list[rel] & 0x7fffffffu) : rel;
+        K.j = (uint32_t)(T.first + (uint64_t)wrel);
+        const int nS = T.q.nS;
+
+        // ---- 1. forward BFS from the seeds (blocked nodes are filtered, not marked) ----
+        for (int i = tid; i < nS; i += BD) {
+            const int s = T.q.S[i];
+            atomicOr(&bm[s >> 5], 1u << (s & 31));
+            Q[i] = s;
+            loc[s] = i;
+            lvl[i] = 0;
+            idom[i] = -1;
+        }
+        __syncthreads();
+        unsigned long long wedges = 0;
+        const Fwd fwd{T.row_ptr, T.ce};
+        const DomRec rec{loc, lvl, idom, pu, pv, lstart, T.q.seed_bm, T.q.blocked_bm, a.ecap};
+        const int tail = bfs<BD, true>(fwd, rec, K, bm, Q, nS, sh, wedges);
+        __syncthreads();
+        const int L = sh.nlev;
+        const int npairs = sh.npairs;
+        const bool big = npairs > a.ecap;
+        bool defer = big;
+
+        if (!big) {
+            // ---- 2. immediate dominators ----
+            for (int k = tid; k < npairs; k += BD) pv[k] = loc[pv[k]];
+            for (int i = tid; i < tail; i += BD) {
+                sz[i] = i < nS ? 0 : 1;
+                cur[i] = 0;
+            }
+            __syncthreads();
+            for (int it = 0;; ++it) {
+                int changed = 0;
+                for (int k = tid; k < npairs; k += BD) {
+                    const int i = pv[k];
+                    if (i < nS) continue;
+                    const int p = pu[k];
+                    int c0 = __ldcg(idom + i);
+                    for (int guard = 0; guard < (1 << 22); ++guard) {
+                        const int c = dt_lca(c0, p, lvl, idom, nS);
+                        if (c == c0) break;
+                        const int old = atomicCAS(idom + i, c0, c);
+                        if (old == c0) {
+                            changed = 1;
+                            break;
+                        }
+                        c0 = old;
+                    }
+                }
+                if (!__syncthreads_or(changed)) break;
+                if (it > (1 << 20)) {
+                    if (tid == 0) atomicOr(T.out.err, DERR_TIMEOUT);
+                    break;
+                }
+            }
+            // ---- 3. subtree sizes, deepest level first ----
+            for (int lv = L - 1; lv >= 1; --lv) {
+                const int s0 = lstart[lv], s1 = lstart[lv + 1];
+                for (int i = s0 + tid; i < s1; i += BD) {
+                    const int d = __ldcg(idom + i);
+                    if (d >= nS) atomicAdd(sz + d, __ldcg(sz + i));
+                }
+                __syncthreads();
+            }
+            if (store) {
+                if (tid == 0)
+                    sh.sbase = reserve_store(T.out.rec_cursor, (unsigned long long)(tail - nS), T.out.rec_cap);
+                __syncthreads();
+                defer = sh.sbase == ~0ull;
+            }
+        }
+
+        if (defer) {
+            if (tid == 0) {
+                const uint32_t d = atomicAdd(T.out.n_deferred, 1u);
+                if (d < T.out.deferred_cap)
+                    T.out.deferred[d] = wrel | (big ? 0x80000000u : 0u);
+                else
+                    atomicOr(T.out.err, DERR_INTERNAL);
+            }
+        } else {
+            // ---- 4. outputs ----
+            if (T.out.credit_L)
+                for (int i = nS + tid; i < tail; i += BD)
+                    atomicAdd(T.out.credit_L + Q[i], (unsigned long long)__ldcg(sz + i));
+            if (store) {
+                const unsigned long long sb = sh.sbase;
+                for (int lv = 1; lv < L; ++lv) {
+                    const int s0 = lstart[lv], s1 = lstart[lv + 1];
+                    for (int i = s0 + tid; i < s1; i += BD) {
+                        const int d = __ldcg(idom + i);
+                        const int size_i = __ldcg(sz + i);
+                        int pr, poff;
+                        if (d < nS) {
+                            pr = atomicAdd(&sh.root, size_i);
+                            poff = 0;
+                        } else {
+                            const int pd = __ldcg(pre + d);
+                            pr = pd + 1 + atomicAdd(cur + d, size_i);
+                            poff = pr - pd;
+                        }
+                        pre[i] = pr;
+                        const unsigned long long r = sb + (unsigned long long)pr;
+                        T.out.rec_node[r] = Q[i];
+                        T.out.rec_par[r] = poff;
+                        T.out.rec_size[r] = size_i;
+                    }
+                    __syncthreads();
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wedges += __shfl_xor_sync(IMIN_FULL, wedges, o);
+            if (lane == 0 && wedges) atomicAdd(&sh.edges, wedges);
+            __syncthreads();
+            if (tid == 0) {
+                atomicAdd(T.out.acc + 0, (unsigned long long)tail);
+                atomicAdd(T.out.acc + 1, sh.edges);
+                atomicAdd(T.out.acc + 4, 1ull);
+                if (T.out.world_spread) T.out.world_spread[wrel] = (uint32_t)tail;
+            }
+            if (T.out.reach)
+                for (int i = tid; i < tail; i += BD) atomicAdd(T.out.reach + Q[i], 1ull);
+        }
+        // ---- clear the visited marks ----
+        if (SMEM_BM) {
+            __syncthreads();
+            for (size_t w = tid; w < a.bm_words; w += BD) s_bm[w] = 0;
+        } else {
+            for (int i = tid; i < tail; i += BD) bm[Q[i] >> 5] = 0;
+        }
+        __syncthreads();
+    }
+}
+
+inline size_t static_smem(int bd, bool lower = false)
+{
+    return (size_t)(4 * BIGCAP + 1 + (lower ? 2 : 1) * (bd / 32) * CAND + 8 + 6 + (lower ? 0 : 1)) * 4 + 16 + 16;
 }
 
 template <int BD, int MINB, bool SMEM, bool STOP, bool UPPER>
@@ -497,10 +802,25 @@ void launch_one(cudaStream_t st, const CArgs &a, int blocks, size_t smem)
     IM_CHECK_LAUNCH();
 }
 
-// kind: 0 reach-only, 1 reach-only with the stopping rule, 2 upper bound
+template <int BD, int MINB, bool SMEM>
+void launch_lower(cudaStream_t st, const CArgs &a, int blocks, size_t smem)
+{
+    auto kern = cta_lower_kernel<BD, MINB, SMEM>;
+    if (smem > 48 * 1024)
+        IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<blocks, BD, smem, st>>>(a);
+    IM_CHECK_LAUNCH();
+}
+
+// kind: 0 reach-only, 1 reach-only with the stopping rule, 2 upper bound, 3 lower bound
 template <int BD, int MINB>
 void launch(cudaStream_t st, const CArgs &a, int blocks, bool smem_bm, int kind, size_t smem)
 {
+    if (kind == 3) {
+        if (smem_bm) launch_lower<BD, MINB, true>(st, a, blocks, smem);
+        else launch_lower<BD, MINB, false>(st, a, blocks, smem);
+        return;
+    }
     if (smem_bm) {
         if (kind == 2) launch_one<BD, MINB, true, false, true>(st, a, blocks, smem);
         else if (kind == 1) launch_one<BD, MINB, true, true, false>(st, a, blocks, smem);
@@ -514,11 +834,15 @@ void launch(cudaStream_t st, const CArgs &a, int blocks, bool smem_bm, int kind,
 
 // resident CTAs per SM (0 if the configuration cannot launch)
 template <int BD, int MINB>
-int occupancy(bool smem_bm, bool upper, size_t smem)
+int occupancy(bool smem_bm, bool upper, bool lower, size_t smem)
 {
     int nb = 0;
     cudaError_t e;
-    if (smem_bm) {
+    if (lower) {
+        auto kern = smem_bm ? cta_lower_kernel<BD, MINB, true> : cta_lower_kernel<BD, MINB, false>;
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BD, smem);
+    } else if (smem_bm) {
         auto kern = upper ? cta_world_kernel<BD, MINB, true, false, true>
                           : cta_world_kernel<BD, MINB, true, true, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -538,10 +862,10 @@ int occupancy(bool smem_bm, bool upper, size_t smem)
 // explicit instantiations live in reach_cta_<BD>.cu
 #define IMIN_REACH_CTA_INSTANTIATE(BD_, MINB_)                                                          \
     template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, int, size_t);             \
-    template int occupancy<BD_, MINB_>(bool, bool, size_t);
+    template int occupancy<BD_, MINB_>(bool, bool, bool, size_t);
 
 #define IMIN_REACH_CTA_EXTERN(BD_, MINB_)                                                               \
     extern template void launch<BD_, MINB_>(cudaStream_t, const CArgs &, int, bool, int, size_t);      \
-    extern template int occupancy<BD_, MINB_>(bool, bool, size_t);
+    extern template int occupancy<BD_, MINB_>(bool, bool, bool, size_t);
 
 }  // namespace reach_cta

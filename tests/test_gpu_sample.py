@@ -86,6 +86,18 @@ def test_theta_zero_and_edgeless(ctx):
     G.free()
 
 
+@pytest.mark.parametrize("mode", [2, 3])
+def test_lower_pairs_overflow_to_large_slots(er1k, monkeypatch, mode):
+    """A 40-pair budget per CTA slot sends most lower-bound worlds to the large-slot
+    pass; the counts are unchanged."""
+    g, S, cfg, G, og = er1k
+    monkeypatch.setenv("IMIN_SLOT_QCAP", "40")
+    got = G.sample(S, theta=2000, key=6, tag=3, mode=mode, per_world=True)
+    monkeypatch.delenv("IMIN_SLOT_QCAP")
+    want = og.sample(S, theta=2000, key=6, tag=3, mode=mode, per_world=True)
+    assert_sample_equal(got, want)
+
+
 def test_deferred_worlds_match(er1k, monkeypatch):
     """A tiny per-warp queue forces most worlds through the large-slot path."""
     g, S, cfg, G, og = er1k
@@ -105,7 +117,8 @@ def hubs30k():
     rng = np.random.default_rng(13)
     B = rng.choice(np.setdiff1d(np.arange(g.n), S), 40, replace=False)
     og = oracle.OracleGraph.from_graph(g)
-    cases = (([], 700, 0, 1), (B, 500, 77_777, 1), ([], 600, 5, 5), (B, 400, 999, 4))
+    cases = (([], 700, 0, 1), (B, 500, 77_777, 1), ([], 600, 5, 5), (B, 400, 999, 4),
+             ([], 300, 11, 3), (B, 300, 4242, 2))
     want = [og.sample(S, b, theta=t, key=3, tag=5, first=f, mode=md, per_world=True)
             for b, t, f, md in cases]
     return g, S, cases, want
@@ -117,14 +130,15 @@ REACH_CONFIGS = ["warp"] + [f"{bd}x{mb}/{w}" for bd, mb in ((256, 4), (256, 8), 
 
 @pytest.mark.parametrize("cfg", REACH_CONFIGS)
 def test_reach_launch_configurations(ctx, monkeypatch, hubs30k, cfg):
-    """Reach-only and upper-bound (LRR) worlds give the same bits under every launch
-    configuration the autotuner may pick: warp-per-world, or a CTA per world of
-    256/512/1024 threads compiled for a given number of CTAs per SM, with the visited
-    bitmap in global (g) or shared (s) memory."""
+    """Reach-only, lower-bound (dominator / CP) and upper-bound (LRR) worlds give the
+    same bits under every launch configuration the autotuner may pick: warp-per-world,
+    or a CTA per world of 256/512/1024 threads compiled for a given number of CTAs per
+    SM, with the visited bitmap in global (g) or shared (s) memory."""
     g, S, cases, want = hubs30k
     if cfg == "warp":
         monkeypatch.setenv("IMIN_REACH_CTA", "0")
         monkeypatch.setenv("IMIN_UPPER_CTA", "0")
+        monkeypatch.setenv("IMIN_LOWER_CTA", "0")
     else:
         shape, where = cfg.split("/")
         bd, mb = shape.split("x")
