@@ -1,0 +1,75 @@
+"""Sharding of the sampling step across ranks (one process per GPU).
+
+Worlds are addressed by index (a world's coins depend only on the key, the stream tag
+and instance, and the world index j; Sec. 2.1 live-edge worlds), so a call over worlds
+[first, first + theta) splits into contiguous sub-ranges with no communication.  Each
+rank samples its own range with the library; one sum all-reduce then merges:
+
+* the per-node count vectors (reach, credit_lower, credit_upper): integers, so the sum
+  does not depend on the split or on the reduction order;
+* the scalar totals (total spread, edges scanned, non-empty LRR sets);
+* the per-world spreads, gathered in world order.
+
+On a box with one GPU per query this runs as independent replicas (``bench.py --gpus
+N``); the merge logic itself is exercised with CPU ranks over the ``gloo`` backend.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+COUNT_KEYS = ("reach", "credit_lower", "credit_upper")
+SCALAR_KEYS = ("total_spread", "edges_scanned", "nonempty_lrr")
+
+
+def world_range(theta: int, rank: int, world_size: int):
+    """(first offset, count) of this rank's contiguous share of [0, theta): the first
+    theta % world_size ranks take one extra world."""
+    if world_size < 1 or not 0 <= rank < world_size:
+        raise ValueError("bad rank / world size")
+    if theta < 0:
+        raise ValueError("negative theta")
+    base, extra = divmod(int(theta), world_size)
+    first = rank * base + min(rank, extra)
+    return first, base + (1 if rank < extra else 0)
+
+
+def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, group=None, **kw):
+    """Run ``sample(S, blocked, theta=count, first=first + offset, per_world=..., **kw)``
+    (for instance ``Graph.sample``) on this rank's share of the worlds and merge the
+    results of all ranks of ``group`` (``torch.distributed``).  Every rank returns the
+    merged result, equal bit for bit to one call over all ``theta`` worlds."""
+    import torch
+    import torch.distributed as dist
+
+    ws = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    off, cnt = world_range(theta, rank, ws)
+    part = sample(S, blocked, theta=cnt, first=int(first) + off, per_world=per_world, **kw)
+    out = {}
+    keys = [k for k in COUNT_KEYS if k in part]
+    # one all-reduce: the count vectors and the scalars in one int64 buffer (every
+    # count is far below 2^63)
+    n = len(part[keys[0]]) if keys else 0
+    buf = np.zeros(len(keys) * n + len(SCALAR_KEYS), dtype=np.int64)
+    for i, k in enumerate(keys):
+        buf[i * n:(i + 1) * n] = np.asarray(part[k], dtype=np.uint64).astype(np.int64)
+    for i, k in enumerate(SCALAR_KEYS):
+        buf[len(keys) * n + i] = int(part.get(k, 0))
+    t = torch.from_numpy(buf)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    buf = t.numpy()
+    for i, k in enumerate(keys):
+        out[k] = buf[i * n:(i + 1) * n].astype(np.uint64)
+    for i, k in enumerate(SCALAR_KEYS):
+        out[k] = int(buf[len(keys) * n + i])
+    if per_world:
+        # every rank's spreads, in world order (ranks hold consecutive ranges)
+        ws_local = torch.from_numpy(np.asarray(part["world_spread"], dtype=np.int64))
+        sizes = [world_range(theta, r, ws)[1] for r in range(ws)]
+        pad = torch.zeros(max(sizes), dtype=torch.int64)
+        pad[:cnt] = ws_local
+        gathered = [torch.zeros_like(pad) for _ in range(ws)]
+        dist.all_gather(gathered, pad, group=group)
+        out["world_spread"] = np.concatenate(
+            [g.numpy()[:s] for g, s in zip(gathered, sizes)]).astype(np.uint32)
+    return out

@@ -63,14 +63,19 @@ def csr_from_edges(n: int, src, dst, prob=None, name: str = "") -> Graph:
     """Sort edges by (src, dst) and build the CSR.  Duplicates are kept."""
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
-    order = np.lexsort((dst, src))
-    src, dst = src[order], dst[order]
+    if src.shape[0] > 1 and np.all((src[1:] > src[:-1]) | ((src[1:] == src[:-1]) & (dst[1:] >= dst[:-1]))):
+        order = None                       # already in (src, dst) order: skip the sort
+    else:
+        order = np.lexsort((dst, src))
+        src, dst = src[order], dst[order]
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(np.bincount(src, minlength=n), out=row_ptr[1:])
     if prob is None:
         prob = np.ones(src.shape[0], dtype=np.float32)
     else:
-        prob = np.asarray(prob, dtype=np.float32)[order]
+        prob = np.asarray(prob, dtype=np.float32)
+        if order is not None:
+            prob = prob[order]
     return Graph(n, row_ptr.astype(np.int32), dst.astype(np.int32), prob, name)
 
 
@@ -85,7 +90,9 @@ def _dedupe(n: int, src, dst):
     """Drop self-loops and repeated (src, dst) pairs; return sorted unique pairs."""
     keep = src != dst
     key = src[keep].astype(np.int64) * n + dst[keep].astype(np.int64)
-    key = np.unique(key)
+    key.sort()                                   # sorted unique keys (as np.unique gives)
+    if key.shape[0] > 1:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     return key // n, key % n
 
 
@@ -155,8 +162,8 @@ def rmat(scale: int = 22, edge_factor: int = 16, a: float = 0.57, b: float = 0.1
         bit = np.int64(1) << (scale - 1 - lvl)
         right = ((r >= t_a) & (r < t_ab)) | (r >= t_abc)   # quadrants b, d
         down = r >= t_ab                                     # quadrants c, d
-        dst += right.astype(np.int64) * bit
-        src += down.astype(np.int64) * bit
+        np.add(dst, bit, out=dst, where=right)
+        np.add(src, bit, out=src, where=down)
         del r, right, down
     perm = rng.permutation(n)
     src = perm[src]
