@@ -366,6 +366,7 @@ def main():
         results.append(r)
     barrier()
     clk = clocks.stop()
+    shape = G.tuning()          # the autotuner's launch shape for reach-only worlds
     step_s = float(np.mean(times))
     if world > 1:
         t = torch.tensor([step_s], device="cuda")
@@ -406,16 +407,22 @@ def main():
     pk = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
     achieved = alg_bytes / kms / 1e9 if kms > 0 else 0.0
+    # DRAM traffic per launch: bytes per algorithmic byte from one ncu capture of the
+    # same kernel and launch shape on a smaller reach-only case, times this launch's
+    # algorithmic bytes (traffic grows with the nodes and edges a launch processes)
     traffic = None
     tp = os.path.join(ROOT, "profiles", "reach_kernel_traffic.json")
     if os.path.exists(tp):
         try:
-            traffic = json.load(open(tp)).get("bytes_per_launch_full_size")
+            tj = json.load(open(tp))
+            if tj.get("shape") == shape:
+                traffic = tj["dram_bytes_per_alg_byte"] * alg_bytes / max(launches, 1)
         except Exception:
             traffic = None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "world_kernel<reach-only, stop rule>",
+            "kernel": "cta_world_kernel<reach-only, stopping rule>",
+            "launch_shape": shape,
             "per_launch_ms": kms * 1e3 / max(launches, 1),
             "algorithmic_bytes": "16 B per reached node + 8 B per scanned edge",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk
