@@ -796,7 +796,7 @@ template <int BD, int MINB, bool SMEM, bool STOP, bool UPPER>
 void launch_one(cudaStream_t st, const CArgs &a, int blocks, size_t smem)
 {
     auto kern = cta_world_kernel<BD, MINB, SMEM, STOP, UPPER>;
-    if (smem > 48 * 1024)
+    if (smem > 0)
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<blocks, BD, smem, st>>>(a);
     IM_CHECK_LAUNCH();
@@ -806,7 +806,7 @@ template <int BD, int MINB, bool SMEM>
 void launch_lower(cudaStream_t st, const CArgs &a, int blocks, size_t smem)
 {
     auto kern = cta_lower_kernel<BD, MINB, SMEM>;
-    if (smem > 48 * 1024)
+    if (smem > 0)
         IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<blocks, BD, smem, st>>>(a);
     IM_CHECK_LAUNCH();
@@ -840,12 +840,12 @@ int occupancy(bool smem_bm, bool upper, bool lower, size_t smem)
     cudaError_t e;
     if (lower) {
         auto kern = smem_bm ? cta_lower_kernel<BD, MINB, true> : cta_lower_kernel<BD, MINB, false>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BD, smem);
     } else if (smem_bm) {
         auto kern = upper ? cta_world_kernel<BD, MINB, true, false, true>
                           : cta_world_kernel<BD, MINB, true, true, false>;
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (smem > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BD, smem);
     } else {
         auto kern = upper ? cta_world_kernel<BD, MINB, false, false, true>

@@ -183,6 +183,26 @@ def test_reach_many_hubs_in_one_level(ctx, monkeypatch, cfg):
     G.free()
 
 
+@pytest.mark.parametrize("shape", ["256x8", "512x4", "1024x2"])
+def test_smem_bitmap_above_default_dynamic_limit(ctx, monkeypatch, shape):
+    """A 300,000-node graph: its visited bitmap (37.5 KB) plus the kernel's static shared
+    memory passes the 48 KB that a launch gets without opting in, while the bitmap alone
+    does not; every mode must still launch and match the oracle."""
+    g = synth.chung_lu_poisson(300_000, 10.0, 2.1, seed=8)
+    S = synth.seeds_top_outdeg(g, 20, 0.01, seed=9)
+    bd, mb = shape.split("x")
+    monkeypatch.setenv("IMIN_REACH_BD", bd)
+    monkeypatch.setenv("IMIN_REACH_MINB", mb)
+    monkeypatch.setenv("IMIN_REACH_SMEM", "1")
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    for mode in (1, 2, 4):
+        got = G.sample(S, theta=60, key=4, tag=6, first=1000, mode=mode, per_world=True)
+        want = og.sample(S, theta=60, key=4, tag=6, first=1000, mode=mode, per_world=True)
+        assert_sample_equal(got, want)
+    G.free()
+
+
 def test_small_chung_lu_hubs(ctx):
     g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
     S = synth.seeds_top_outdeg(g, 20, 0.01, seed=4)
