@@ -365,12 +365,15 @@ struct Runner {
         }
     }
 
+    // The slot arena is prepared last, after every other allocation of the launch: an
+    // allocation that does not fit drops the (cached) arenas, see dev_alloc.
     void launch(const std::vector<WTask> &ht, const imin_graph *g0, uint32_t flags,
-                const SlotCfg &cfg, DBuf &arena)
+                const SlotCfg &cfg, DBuf &arena, size_t &layout)
     {
         const int n = (int)ht.size();
         dtasks.ensure(ctx, ht.size() * sizeof(WTask));
         cd.ensure(ctx, (size_t)n * 8 + 16);
+        prepare_slots(arena, cfg, layout);
         IM_CUDA(cudaMemcpyAsync(dtasks.p, ht.data(), ht.size() * sizeof(WTask), cudaMemcpyHostToDevice,
                                 ctx->stream));
         IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)n * 8, ctx->stream));
@@ -415,11 +418,10 @@ struct Runner {
         SlotCfg cfg = cfg_for(flags, nmax, mmax, nSmax, false);
         DBuf &arena = cfg.lower ? ctx->slots_lower : ctx->slots;
         size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
-        prepare_slots(arena, cfg, layout);
         std::vector<WTask> ht;
         for (int i = 0; i < n; ++i)
             ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, nullptr, T[i]->out));
-        launch(ht, T[0]->g, flags, cfg, arena);
+        launch(ht, T[0]->g, flags, cfg, arena, layout);
         std::vector<unsigned char> hc((size_t)n * CTL);
         std::vector<uint32_t> claims(n);
         IM_CUDA(cudaMemcpy(claims.data(), cd.p, (size_t)n * 4, cudaMemcpyDeviceToHost));
@@ -466,11 +468,10 @@ struct Runner {
                     at += L[i].size();
                 }
                 if (pass == 0) {
-                    launch(lt, T[0]->g, flags, cfg, arena);
+                    launch(lt, T[0]->g, flags, cfg, arena, layout);
                 } else {
                     SlotCfg bc = cfg_for(flags, nmax, mmax, nSmax, true);
-                    prepare_slots(ctx->big_slots, bc, ctx->big_slots_layout);
-                    launch(lt, T[0]->g, flags, bc, ctx->big_slots);
+                    launch(lt, T[0]->g, flags, bc, ctx->big_slots, ctx->big_slots_layout);
                 }
             }
             IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));

@@ -16,15 +16,35 @@ unsigned long long g_kernel_launches = 0;
 // ---------------------------------------------------------------------------
 // device memory accounting
 // ---------------------------------------------------------------------------
+// The world-kernel slot arenas are caches sized from the free memory at the time of a
+// launch; when an allocation does not fit they are dropped (cudaFree waits for the
+// device) and re-sized by the next launch.  Returns whether anything was freed.
+static bool trim_slot_arenas(imin_ctx *ctx)
+{
+    bool any = false;
+    for (DBuf *b : {&ctx->slots, &ctx->slots_lower, &ctx->big_slots})
+        if (b->p) {
+            b->release();
+            any = true;
+        }
+    ctx->slots_layout = ctx->slots_lower_layout = ctx->big_slots_layout = 0;
+    return any;
+}
+
 void *dev_alloc(imin_ctx *ctx, size_t bytes)
 {
     if (bytes == 0) return nullptr;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget) trim_slot_arenas(ctx);
     if (ctx->budget && ctx->in_use + bytes > ctx->budget)
         throw ImError{IMIN_ENOMEM, "device memory budget exceeded (" + std::to_string(ctx->in_use) +
                                        " + " + std::to_string(bytes) + " > " +
                                        std::to_string(ctx->budget) + " bytes)"};
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        if (trim_slot_arenas(ctx)) e = cudaMalloc(&p, bytes);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw ImError{IMIN_ENOMEM, std::string("cudaMalloc(") + std::to_string(bytes) +
