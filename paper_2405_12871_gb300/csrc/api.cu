@@ -1427,8 +1427,32 @@ void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
     Timer total;
     const unsigned long long launches0 = g_kernel_launches;
     Scheduler sch(ctx);
-    for (Inst *I : all) sch.add(I);
-    while (!sch.active.empty()) sch.step();
+    // Instances are admitted as a rolling window: at most `cap` in flight (each holds
+    // its sample stores until it finishes), and a new one only while at least a quarter
+    // of the device memory is free (the slot arenas count as free: they are caches).
+    int cap = 64;
+    if (const char *env = std::getenv("IMIN_BATCH_ACTIVE")) {
+        const long v = std::strtol(env, nullptr, 10);
+        if (v >= 1) cap = (int)v;
+    }
+    size_t next = 0;
+    auto admit = [&]() {
+        while (next < all.size() && (int)sch.active.size() < cap) {
+            if (!sch.active.empty()) {
+                size_t freeb = 0, totalb = 0;
+                cudaMemGetInfo(&freeb, &totalb);
+                cudaGetLastError();
+                freeb += ctx->slots.bytes + ctx->slots_lower.bytes + ctx->big_slots.bytes;
+                if (freeb < totalb / 4) break;
+            }
+            sch.add(all[next++]);
+        }
+    };
+    admit();
+    while (!sch.active.empty()) {
+        sch.step();
+        admit();
+    }
     sch.ms[7] = total.ms();
     sch.ms[6] = sch.ms[7] - sch.ms[0] - sch.ms[1] - sch.ms[2] - sch.ms[3] - sch.ms[4] - sch.ms[5];
     // stage times and device times belong to the whole batch: every result reports them

@@ -54,7 +54,12 @@ def test_mixed_batch_equals_alone_and_oracle(ctx):
         G.free()
 
 
-def test_batch_of_many_small_instances(ctx):
+@pytest.mark.parametrize("window", [None, "3"])
+def test_batch_of_many_small_instances(ctx, monkeypatch, window):
+    """All ten instances in flight at once, or a rolling window of three admitted as
+    others finish: the results equal the one-at-a-time solves either way."""
+    if window:
+        monkeypatch.setenv("IMIN_BATCH_ACTIVE", window)
     gs = [synth.chung_lu(int(n), 10.0, 2.1, seed=20 + i)
           for i, n in enumerate(np.geomspace(1000, 30_000, 10).astype(int))]
     Gs = [ctx.load_graph(g) for g in gs]
