@@ -198,8 +198,12 @@ def run_batch(args):
     batched = ctx.solve_batch(qs)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - a
-    same = all(list(x["blockers"]) == list(y["blockers"]) and x["I_after"] == y["I_after"]
-               for x, y in zip(plain, batched))
+    diff = [i for i, (x, y) in enumerate(zip(plain, batched))
+            if not (list(x["blockers"]) == list(y["blockers"]) and x["I_after"] == y["I_after"])]
+    same = not diff
+    for i in diff[:8]:
+        print(json.dumps({"batch_mismatch": i, "n": items[i][0].n, "plain_I_after": plain[i]["I_after"],
+                          "batched_I_after": batched[i]["I_after"]}), file=sys.stderr, flush=True)
     line = {"mode": "batch", "instances": len(items), "plain_s": t_plain, "batched_s": t_batch,
             "speedup": t_plain / t_batch, "plain_inst_per_s": len(items) / t_plain,
             "batched_inst_per_s": len(items) / t_batch, "identical_results": same,

@@ -467,11 +467,14 @@ struct Runner {
                                            lists.as<uint32_t>() + at, T[i]->out));
                     at += L[i].size();
                 }
+                // a deferred world was claimed before the early exit, so it must complete:
+                // the re-runs never apply the stopping rule
+                const uint32_t rflags = flags & ~(uint32_t)WF_STOP;
                 if (pass == 0) {
-                    launch(lt, T[0]->g, flags, cfg, arena, layout);
+                    launch(lt, T[0]->g, rflags, cfg, arena, layout);
                 } else {
-                    SlotCfg bc = cfg_for(flags, nmax, mmax, nSmax, true);
-                    launch(lt, T[0]->g, flags, bc, ctx->big_slots, ctx->big_slots_layout);
+                    SlotCfg bc = cfg_for(rflags, nmax, mmax, nSmax, true);
+                    launch(lt, T[0]->g, rflags, bc, ctx->big_slots, ctx->big_slots_layout);
                 }
             }
             IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));

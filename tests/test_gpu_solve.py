@@ -149,3 +149,26 @@ def test_store_growth_path(ctx, monkeypatch):
     G.free()
     monkeypatch.delenv("IMIN_STORE_TIGHT")
     compare(got, og.solve(S, **kw))
+
+
+@pytest.mark.parametrize("chunk", [None, "997"])
+def test_stopping_rule_with_deferred_worlds(ctx, monkeypatch, chunk):
+    """Warp-per-world kernels with a 40-node queue: most stopping-rule worlds overflow
+    their slot and are re-run on large slots after the early exit has fired.  A world
+    claimed before the exit must still complete, so N and every estimate stay the
+    oracle's."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
+    S = synth.seeds_top_outdeg(g, 10, 0.01, seed=4)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=8, eps=0.3, delta=1.0 / g.n, key=11)
+    for var in ("IMIN_REACH_CTA", "IMIN_UPPER_CTA", "IMIN_LOWER_CTA"):
+        monkeypatch.setenv(var, "0")
+    monkeypatch.setenv("IMIN_SLOT_QCAP", "40")
+    if chunk:
+        monkeypatch.setenv("IMIN_STOP_CHUNK", chunk)
+    G = ctx.load_graph(g)
+    got = G.solve(S, **kw)
+    G.free()
+    for var in ("IMIN_SLOT_QCAP", "IMIN_STOP_CHUNK"):
+        monkeypatch.delenv(var, raising=False)
+    compare(got, og.solve(S, **kw))
