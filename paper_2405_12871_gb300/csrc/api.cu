@@ -583,21 +583,29 @@ void autotune_reach(imin_ctx *ctx, imin_graph *g, const Query &q)
         }
         const uint32_t concurrent = cd.warp_per_sm ? (uint32_t)(ctx->num_sms * cd.warp_per_sm)
                                                    : (uint32_t)cd.ctas;
-        const uint32_t W = std::min<uint32_t>(std::max<uint32_t>(2 * std::max(concurrent, widest), 2048), 16384);
-        // an untimed wave loads the kernel, then W and 2W worlds
-        double ms[3] = {0.0, 0.0, 0.0};
-        for (int pass = 0; pass < 3; ++pass) {
+        auto timed = [&](uint32_t count, uint32_t inst) {
             TaskRun t;
             t.g = g;
-            t.q = qdev(q, 0x5eedull, 0xFFFFFFF0u, (uint32_t)pass);
+            t.q = qdev(q, 0x5eedull, 0xFFFFFFF0u, inst);
             t.first = 0;
-            t.count = pass == 0 ? std::min<uint32_t>(concurrent, 1024) : (uint32_t)pass * W;
+            t.count = count;
             std::vector<TaskRun *> tp{&t};
             const double before = probe_runner.kernel_ms;
             probe_runner.gref = g;
             probe_runner.run(tp, 0u);
-            ms[pass] = probe_runner.kernel_ms - before;
+            return probe_runner.kernel_ms - before;
+        };
+        // an untimed wave loads the kernel; then W and 2W worlds, with W at least two
+        // waves and large enough that W worlds take a few milliseconds (small worlds
+        // would otherwise be timed at the resolution of the events)
+        timed(std::min<uint32_t>(concurrent, 1024), 0);
+        uint64_t W = std::min<uint32_t>(std::max<uint32_t>(2 * std::max(concurrent, widest), 2048), 16384);
+        double ms[3] = {0.0, timed((uint32_t)W, 1), 0.0};
+        if (ms[1] < 3.0) {
+            W = std::min<uint64_t>(W * (uint64_t)std::ceil(3.0 / std::max(ms[1], 0.01)), (uint64_t)1 << 20);
+            ms[1] = timed((uint32_t)W, 1);
         }
+        ms[2] = timed((uint32_t)(2 * W), 2);
         const double per_world = ms[2] > ms[1] ? (ms[2] - ms[1]) / W : ms[2] / (2.0 * W);
         if (per_world < best) {
             best = per_world;
