@@ -42,6 +42,7 @@ struct CArgs {
     size_t off_loc, off_lvl, off_idom, off_sz, off_pre, off_cur, off_lstart, off_pu, off_pv;
     int ecap;
     uint32_t flags;
+    int l2_keep;   // group records loaded with the evict-last L2 policy
 };
 
 constexpr int BIG = 32;       // nodes with more items are expanded in phase 2
@@ -134,10 +135,33 @@ struct Coins {
 };
 
 // Forward items: the 4-edge groups of a node's out-edges [b, e).
+// L2 cache policy for the graph's group records: with `keep`, evict-last (the records
+// are re-read by every world in flight, the visited bitmaps and queues are not), else
+// the normal policy.
+__device__ __forceinline__ uint64_t graph_l2_policy(bool keep)
+{
+    uint64_t pol;
+    if (keep)
+        asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint4 ld_group_half(const void *p, uint64_t pol)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+
 struct Fwd {
     static constexpr bool kCountEdges = true;   // the scanned edges are reported
     const int32_t *row_ptr;
     const uint4 *ce;
+    uint64_t pol;   // L2 policy of the group loads
     __device__ __forceinline__ void range(int u, int &b, int &e) const
     {
         b = row_ptr[u];
@@ -148,9 +172,10 @@ struct Fwd {
     // live in-range edges of group g as a 4-bit mask, their targets in c4
     __device__ __forceinline__ uint32_t live(int g, int ob, int oe, const Coins &K, int4 &c4) const
     {
-        const int4 *p = reinterpret_cast<const int4 *>(ce + 2 * (size_t)g);
-        c4 = __ldg(p);
-        const uint4 t4 = __ldg(reinterpret_cast<const uint4 *>(p + 1));
+        const uint4 *p = ce + 2 * (size_t)g;
+        const uint4 cu = ld_group_half(p, pol);
+        c4 = make_int4((int)cu.x, (int)cu.y, (int)cu.z, (int)cu.w);
+        const uint4 t4 = ld_group_half(p + 1, pol);
         const uint4 w = philox10_w(make_uint4((uint32_t)g, K.j, K.tag, K.inst), K.klo, K.khi);
         uint32_t m = (uint32_t)((w.x >> 8) < t4.x) | ((uint32_t)((w.y >> 8) < t4.y) << 1) |
                      ((uint32_t)((w.z >> 8) < t4.z) << 2) | ((uint32_t)((w.w >> 8) < t4.w) << 3);
@@ -472,7 +497,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
         }
         __syncthreads();
         unsigned long long wedges = 0;
-        const Fwd fwd{T.row_ptr, T.ce};
+        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0)};
         const int tail = bfs<BD, false>(fwd, NoRec{}, K, bm, Q, nS, sh, wedges);
 
         // ---- upper bound: target from V'_s, reverse BFS inside the reached set ----
@@ -667,7 +692,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_lower_kernel(const CArgs a)
         }
         __syncthreads();
         unsigned long long wedges = 0;
-        const Fwd fwd{T.row_ptr, T.ce};
+        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0)};
         const DomRec rec{loc, lvl, idom, pu, pv, lstart, T.q.seed_bm, T.q.blocked_bm, a.ecap};
         const int tail = bfs<BD, true>(fwd, rec, K, bm, Q, nS, sh, wedges);
         __syncthreads();

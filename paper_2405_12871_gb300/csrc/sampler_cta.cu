@@ -2,6 +2,8 @@
 // layout, occupancy and the dispatch over CTA size and CTAs per SM.
 #include "reach_cta.cuh"
 
+#include <cstdlib>
+
 namespace reach_cta {
 IMIN_REACH_CTA_EXTERN(256, 4)
 IMIN_REACH_CTA_EXTERN(256, 8)
@@ -104,6 +106,12 @@ void launch_cta_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t 
     a.bm_words = cfg.bm_words;
     cta_layout(cfg, &a, nullptr);
     a.flags = flags;
+    // tuning knob: IMIN_L2_KEEP=0 loads the graph's group records with the normal L2
+    // policy instead of evict-last
+    {
+        const char *env = std::getenv("IMIN_L2_KEEP");
+        a.l2_keep = (env && env[0] == '0') ? 0 : 1;
+    }
     const int kind = (flags & WF_LOWER) ? 3 : ((flags & WF_UPPER) ? 2 : ((flags & WF_STOP) ? 1 : 0));
     const size_t smem = cfg.smem_bm ? cfg.bm_words * 4 : 0;
     const int bd = cfg.cta_threads, mb = cfg.cta_minb;
