@@ -266,6 +266,45 @@ def run_batch(args):
     return 0 if same else 1
 
 
+def run_baselines(args):
+    """SandIMIN against the dominator-tree baselines AG and GR on the CL-1M query: solve
+    time, blockers, and the spread left by each blocker set, re-estimated on the same
+    independent worlds (stream tag 9, which no solve uses)."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, baselines, synth
+    g, S, cfg = synth.workload_cl1m()
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    G = ctx.load_graph(g)
+    kw = dict(k=cfg["k"], eps=cfg["eps"], delta=cfg["delta"], key=cfg["key"])
+    G.solve(S, **kw)                              # warm-up (autotuner, arenas)
+    torch.cuda.synchronize()
+    out = {"mode": "baselines", "workload": "chung-lu-1M", "k": cfg["k"], "theta_per_estimate": args.baseline_theta,
+           "eval_worlds": args.baseline_eval}
+    t = time.perf_counter()
+    r = G.solve(S, **kw)
+    torch.cuda.synchronize()
+    sets = {"sandimin": ([int(x) for x in r["blockers"]], time.perf_counter() - t, None)}
+    for name, fn in (("ag", lambda: baselines.advanced_greedy(G.sample, g.n, S, cfg["k"], args.baseline_theta)),
+                     ("gr", lambda: baselines.greedy_replace(G.sample, g, S, cfg["k"], args.baseline_theta))):
+        t = time.perf_counter()
+        B, calls, worlds = fn()
+        torch.cuda.synchronize()
+        sets[name] = (B, time.perf_counter() - t, {"estimates": calls, "worlds": worlds})
+    for name, (B, sec, extra) in sets.items():
+        ev = G.sample(S, B, theta=args.baseline_eval, key=1, tag=9, mode=0, per_world=True)
+        ws = ev["world_spread"].astype(np.float64)
+        out[name] = {"seconds": sec, "blockers": len(B), "spread": float(ws.mean()),
+                     "spread_stderr": float(ws.std(ddof=1) / np.sqrt(len(ws)))}
+        if extra:
+            out[name].update(extra)
+    ev0 = G.sample(S, (), theta=args.baseline_eval, key=1, tag=9, mode=0)
+    out["spread_without_blockers"] = ev0["total_spread"] / args.baseline_eval
+    print(json.dumps(out), flush=True)
+    G.free()
+    ctx.close()
+    return 0
+
+
 def run_serve(args):
     """Poisson stream through the server; the same stream replayed one query at a time
     (first come, first served) gives the plain latency and throughput."""
@@ -347,6 +386,12 @@ def main():
                          "continuous-batching server vs a plain one-at-a-time replay")
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--baselines", action="store_true",
+                    help="SandIMIN vs the AG and GR baselines on the CL-1M query")
+    ap.add_argument("--baseline-theta", type=int, default=10_000,
+                    help="worlds per AG / GR estimate")
+    ap.add_argument("--baseline-eval", type=int, default=100_000,
+                    help="worlds of the final spread re-estimate")
     ap.add_argument("--reach-only-worlds", type=int, default=0,
                     help="profiling case: run two imin_sample launches of this many reach-only "
                          "worlds on the same workload (the stopping rule's kernel) and exit")
@@ -360,6 +405,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.baselines:
+        return run_baselines(args)
 
     import torch
     import torch.distributed as dist
