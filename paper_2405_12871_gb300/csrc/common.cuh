@@ -1,13 +1,16 @@
 // common.cuh -- internal declarations shared by the library's translation units.
 //
 // Device-side layout (all resident in HBM):
-//   graph:  row_ptr int32[n+1]; col int32[m4]; thr uint32[m4] (m4 = m rounded up to a
-//           multiple of 4, padding thr = 0), so that one 16-byte load brings the 4 edges
-//           of one Philox counter group;  reverse index in_ptr int32[n+1], in_src int32[m],
-//           in_eid int32[m], in_thr uint32[m] (thr of the forward edge, for coalescing).
-//   slots:  one per resident warp of the world kernel (a warp traverses one world at a
-//           time): visited bitmap (n bits), BFS queue (qcap), and for the lower bound
-//           node->local map (n), per-local arrays (qcap) and live-edge pairs (ecap).
+//   graph:  row_ptr int32[n+1]; ce: one 32-byte record per 4-edge Philox counter group
+//           (4 targets, 4 coin thresholds; m rounded up to a multiple of 4, padding
+//           threshold 0); col int32[m4] and thr uint32[m4] flat copies; reverse index
+//           in_ptr int32[n+1], in_src int32[m], in_eid int32[m], in_thr uint32[m] (thr of
+//           the forward edge, for coalescing).
+//   slots:  one per world in flight.  CTA-per-world kernels (reach_cta.cuh): one slot
+//           per resident CTA (visited bitmap unless it is in shared memory, queue of n + 1,
+//           and the bound's arrays).  Warp-per-world kernel (sampler.cu): one slot per
+//           resident warp (bitmap, queue of qcap, lower-bound arrays of qcap and ecap);
+//           worlds that overflow are re-run on large slots.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -1,4 +1,7 @@
-// sampler.cu -- the world kernel: one warp traverses one live-edge world at a time.
+// sampler.cu -- the warp-per-world kernel: one warp traverses one live-edge world at a
+// time.  The CTA-per-world kernels (reach_cta.cuh) compute the same counts and are the
+// default; this kernel remains an autotuner candidate (small worlds), serves worlds that
+// carry both bounds at once, and runs the large-slot pass for worlds that overflow.
 //
 // Per world j (Sec. 2.1, Algorithms 2 and 3):
 //   1. masked reach BFS from the seed set (the unified seed s of Sec. 3.1 is the
