@@ -305,6 +305,35 @@ def run_baselines(args):
     return 0
 
 
+def run_sweep(args):
+    """Effectiveness sweeps on the CL-1M stand-in (analogues of the paper's eps, |S| and
+    k sweeps): for each setting, solve time, the estimated spread before and after each
+    candidate's blockers, the chosen candidate and the approximation-ratio lower bound."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    g, S50, cfg = synth.workload_cl1m()
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    G = ctx.load_graph(g)
+    G.solve(S50, k=cfg["k"], eps=cfg["eps"], delta=cfg["delta"])     # warm-up
+    settings = [("eps", e, 50, 100) for e in (0.1, 0.2, 0.3)]
+    settings += [("k", e, 50, k) for e, k in ((0.1, 25), (0.1, 50), (0.1, 200))]
+    settings += [("seeds", 0.1, s, 100) for s in (10, 100)]
+    rows = []
+    for what, eps, ns, k in settings:
+        S = S50 if ns == 50 else synth.seeds_top_outdeg(g, ns, 0.01, seed=2)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = G.solve(S, k=k, eps=eps, delta=cfg["delta"])
+        torch.cuda.synchronize()
+        rows.append({"sweep": what, "eps": eps, "seeds": ns, "k": k, "seconds": time.perf_counter() - t,
+                     "I_hat": r["I_hat"], "I_after": list(r["I_after"]), "chosen": "LUR"[r["chosen"]],
+                     "ratio_lb": r["ratio_lb"], "worlds": int(r["worlds_sampled"])})
+    print(json.dumps({"mode": "sweep", "workload": "chung-lu-1M", "delta": "1/n", "rows": rows}), flush=True)
+    G.free()
+    ctx.close()
+    return 0
+
+
 def run_serve(args):
     """Poisson stream through the server; the same stream replayed one query at a time
     (first come, first served) gives the plain latency and throughput."""
@@ -386,6 +415,8 @@ def main():
                          "continuous-batching server vs a plain one-at-a-time replay")
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--sweep", action="store_true",
+                    help="eps / |S| / k sweeps of the solve on the CL-1M stand-in")
     ap.add_argument("--baselines", action="store_true",
                     help="SandIMIN vs the AG and GR baselines on the CL-1M query")
     ap.add_argument("--baseline-theta", type=int, default=10_000,
@@ -407,6 +438,8 @@ def main():
         return run_serve(args)
     if args.baselines:
         return run_baselines(args)
+    if args.sweep:
+        return run_sweep(args)
 
     import torch
     import torch.distributed as dist
