@@ -22,6 +22,7 @@
 #include "greedy.cuh"
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -697,10 +698,27 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
             idx.push_back(i);
         }
         if (tp.empty()) break;
-        Runner run(ctx);
-        run.run(tp, WF_STOP | WF_SPREAD);
-        kms += run.kernel_ms;
-        launches += (uint64_t)run.launches;
+        // estimates on graphs that the autotuner gave different launch shapes run in
+        // separate launches, each in its graph's shape (one launch when they agree)
+        std::vector<std::vector<TaskRun *>> groups;
+        std::vector<std::array<int, 4>> keys;
+        for (TaskRun *t : tp) {
+            const std::array<int, 4> key{t->g->tuned_ctas, t->g->tuned_bd, t->g->tuned_minb,
+                                         t->g->tuned_smem ? 1 : 0};
+            size_t gi = 0;
+            while (gi < keys.size() && keys[gi] != key) ++gi;
+            if (gi == keys.size()) {
+                keys.push_back(key);
+                groups.emplace_back();
+            }
+            groups[gi].push_back(t);
+        }
+        for (std::vector<TaskRun *> &grp : groups) {
+            Runner run(ctx);
+            run.run(grp, WF_STOP | WF_SPREAD);
+            kms += run.kernel_ms;
+            launches += (uint64_t)run.launches;
+        }
         for (size_t i : idx) {
             // every claimed world is complete (deferred ones were re-run)
             const uint64_t want = tr[i].claimed_main;
