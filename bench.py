@@ -532,7 +532,9 @@ def main():
         e2e = {"value": float(np.mean(e2e_t)), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
                "what": "imin_load_graph from host CSR + imin_solve + imin_free_graph",
-               "host_buffers": "pinned" if pinned else "pageable"}
+               "host_buffers": ("pinned caller buffers; prob is copied to the device from them, row_ptr "
+                                "and col through the library's own host copies (kept for the host controller)")
+               if pinned else "pageable"}
         assert list(r2["blockers"]) == list(results[-1]["blockers"])
 
     # ---- throughput and roofline of the dominant kernel (reach-only world kernel) ----
