@@ -172,3 +172,24 @@ def test_stopping_rule_with_deferred_worlds(ctx, monkeypatch, chunk):
     for var in ("IMIN_SLOT_QCAP", "IMIN_STOP_CHUNK"):
         monkeypatch.delenv(var, raising=False)
     compare(got, og.solve(S, **kw))
+
+
+@pytest.mark.parametrize("which", ["opt", "lhga", "ratio"])
+def test_controller_pin_graphs(ctx, which):
+    """The graphs whose OPT^L, LHGA order and approximation-ratio bound are worked out
+    by hand: the library gives the oracle's results on them, bit for bit."""
+    import pin_graphs
+    if which == "opt":
+        g, S, kws = pin_graphs.opt_graph(), pin_graphs.OPT_S, [dict(k=4, variant="lsbm"),
+                                                               dict(k=4)]
+    elif which == "lhga":
+        g, S = pin_graphs.lhga_graph()[0], [0]
+        kws = [dict(k=k, variant="lhga") for k in (1, 2, 3)]
+    else:
+        g, S, kws = pin_graphs.ratio_graph(), [0], [dict(k=1), dict(k=1, variant="sandimin-")]
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    for kw in kws:
+        kw = dict(kw, eps=0.2, delta=0.05)
+        compare(G.solve(S, **kw), og.solve(S, **kw))
+    G.free()
