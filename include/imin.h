@@ -295,14 +295,24 @@ void imin_last_error(imin_ctx *ctx, char *buf, size_t len);
  *   d_world_spread            DEVICE uint32[theta] or NULL; |R_j| per world
  *   totals                    HOST uint64[2]: total spread, edges scanned
  *   stream                    cudaStream_t of the caller's device (NULL = legacy default)
+ * The device arrays cannot be checked before the launch; the kernel checks each
+ * value it uses (row_ptr pairs within [0, m] and non-decreasing, targets in
+ * [0, n), probabilities in [0, 1] and not NaN), skips a bad one without reading
+ * or writing through it, and the call then returns IMIN_EINVAL with d_reach,
+ * d_world_spread and totals unspecified.  Seeds are checked on the host.
+ * Throughput: one 8-warp CTA of scratch slots holds n bits plus n + 1 int32 per
+ * warp, so the number of worlds in flight falls with n: 8 per SM for small
+ * graphs, but at n = 2,000,000 only 8 warps (one CTA) run on the whole GPU,
+ * roughly two orders of magnitude below imin_sample on the same graph.
  * The first call made with a given device current looks up the array's device
  * address (cudaGetSymbolAddress) and keeps it; make that first call before any
  * stream capture.  Every call reuses the same array and clears what must start
  * at zero; calls whose GPU work overlaps (other streams, other host threads)
  * race on the array and must be serialised by the caller.  The call returns
  * after its work has completed.
- * Errors: IMIN_EINVAL (NULL pointer, bad seeds), IMIN_ERANGE (n above the
- * maximum, more than 1024 seeds, world index >= 2^32), IMIN_EDEVICE. */
+ * Errors: IMIN_EINVAL (NULL pointer, bad seeds, invalid device arrays found by
+ * the kernel), IMIN_ERANGE (n above the maximum, more than 1024 seeds, world
+ * index >= 2^32), IMIN_EDEVICE. */
 #define IMIN_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
 #define IMIN_NOALLOC_MAX_NODES 2000000
 int imin_sample_reach_noalloc(const int32_t *d_row_ptr, const int32_t *d_col, const float *d_prob,

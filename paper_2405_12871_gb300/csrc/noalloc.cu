@@ -17,6 +17,12 @@
 // contents, so each call clears the part that must start at zero; two calls whose
 // work overlaps on the GPU (on different streams, or from two host threads) race
 // on it and must be serialised by the caller.
+//
+// The graph arrays live in the caller's device memory, so the host cannot check them
+// before the launch.  The kernel checks every value it uses instead: a row_ptr pair
+// outside [0, m] or decreasing, a target outside [0, n), or a probability that is NaN
+// or outside [0, 1] is skipped (nothing is read or written through it) and sets an
+// error word that the host turns into IMIN_EINVAL.
 #include "common.cuh"
 
 #include <algorithm>
@@ -38,9 +44,12 @@ void *g_base[256] = {nullptr};   // device address of g_noalloc_scratch, per dev
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+constexpr size_t ERR_OFF = 128;                              // uint32 error word
+
 struct NArgs {
     const int32_t *row_ptr, *col;
     const float *prob;
+    int64_t m;
     int32_t n;
     int32_t nS;
     uint64_t first;
@@ -80,6 +89,7 @@ __global__ void __launch_bounds__(256) noalloc_reach_kernel(const NArgs a)
     const size_t wid = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(a.base);   // [0] nodes [1] edges
     uint32_t *claim = reinterpret_cast<uint32_t *>(a.base + 64);
+    uint32_t *err = reinterpret_cast<uint32_t *>(a.base + ERR_OFF);
     const int32_t *S = reinterpret_cast<const int32_t *>(a.base + SEEDS_OFF);
     unsigned char *slot = a.base + SLOTS_OFF + wid * a.slot_bytes;
     uint32_t *bm = reinterpret_cast<uint32_t *>(slot);
@@ -107,6 +117,10 @@ __global__ void __launch_bounds__(256) noalloc_reach_kernel(const NArgs a)
                     const int u = Q[i];
                     b = a.row_ptr[u];
                     e = a.row_ptr[u + 1];
+                    if (b < 0 || e < b || (int64_t)e > a.m) {   // invalid row: skip it
+                        atomicOr(err, 1u);
+                        b = e = 0;
+                    }
                     if (e > b) cnt = ((e + 3) >> 2) - (b >> 2);
                     wedges += (unsigned long long)(e - b);
                 }
@@ -132,8 +146,17 @@ __global__ void __launch_bounds__(256) noalloc_reach_kernel(const NArgs a)
                         for (int c = 0; c < 4; ++c) {
                             const int ec = (g << 2) + c;
                             if (ec < ob || ec >= oe) continue;
-                            if ((wv[c] >> 8) >= n_thr(a.prob[ec])) continue;
+                            const float pe = a.prob[ec];
+                            if (!(pe >= 0.0f && pe <= 1.0f)) {   // NaN or outside [0, 1]
+                                atomicOr(err, 2u);
+                                continue;
+                            }
+                            if ((wv[c] >> 8) >= n_thr(pe)) continue;
                             const int v = a.col[ec];
+                            if (v < 0 || v >= a.n) {
+                                atomicOr(err, 4u);
+                                continue;
+                            }
                             const uint32_t bit = 1u << (v & 31);
                             if (!(atomicOr(&bm[v >> 5], bit) & bit)) nv[c] = v;
                         }
@@ -181,7 +204,8 @@ extern "C" int imin_sample_reach_noalloc(const int32_t *d_row_ptr, const int32_t
     if (n < 1 || m < 0 || nS < 1) return IMIN_EINVAL;
     if (n > IMIN_NOALLOC_MAX_NODES || m >= (int64_t)0x7fffffff - 4 || nS > NOALLOC_MAX_SEEDS)
         return IMIN_ERANGE;
-    if (theta >= ((uint64_t)1 << 32) || first_sample + theta > ((uint64_t)1 << 32)) return IMIN_ERANGE;
+    // world indices must stay below 2^32 (written so that the sum cannot wrap)
+    if (theta >= ((uint64_t)1 << 32) || first_sample > ((uint64_t)1 << 32) - theta) return IMIN_ERANGE;
     for (int32_t i = 0; i < nS; ++i) {
         if (S[i] < 0 || S[i] >= n) return IMIN_EINVAL;
         for (int32_t k = 0; k < i; ++k)
@@ -234,6 +258,7 @@ extern "C" int imin_sample_reach_noalloc(const int32_t *d_row_ptr, const int32_t
         a.row_ptr = d_row_ptr;
         a.col = d_col;
         a.prob = d_prob;
+        a.m = m;
         a.n = n;
         a.nS = nS;
         a.first = first_sample;
@@ -252,12 +277,15 @@ extern "C" int imin_sample_reach_noalloc(const int32_t *d_row_ptr, const int32_t
         if (cudaGetLastError() != cudaSuccess) return IMIN_EDEVICE;
     }
     unsigned long long h[2] = {0, 0};
+    uint32_t herr = 0;
     e = cudaMemcpyAsync(h, base, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, base + ERR_OFF, sizeof(herr), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return IMIN_EDEVICE;
     }
+    if (herr) return IMIN_EINVAL;
     totals[0] = h[0];
     totals[1] = h[1];
     return IMIN_OK;

@@ -33,6 +33,17 @@ def world_range(theta: int, rank: int, world_size: int):
     return first, base + (1 if rank < extra else 0)
 
 
+def collective_device(group=None):
+    """Where a collective buffer must live: the rank's current CUDA device under NCCL
+    (which only moves device memory), the host under gloo."""
+    import torch
+    import torch.distributed as dist
+
+    if dist.get_backend(group) == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, group=None, **kw):
     """Run ``sample(S, blocked, theta=count, first=first + offset, per_world=..., **kw)``
     (for instance ``Graph.sample``) on this rank's share of the worlds and merge the
@@ -43,6 +54,7 @@ def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, gro
 
     ws = dist.get_world_size(group)
     rank = dist.get_rank(group)
+    dev = collective_device(group)
     off, cnt = world_range(theta, rank, ws)
     part = sample(S, blocked, theta=cnt, first=int(first) + off, per_world=per_world, **kw)
     out = {}
@@ -55,9 +67,9 @@ def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, gro
         buf[i * n:(i + 1) * n] = np.asarray(part[k], dtype=np.uint64).astype(np.int64)
     for i, k in enumerate(SCALAR_KEYS):
         buf[len(keys) * n + i] = int(part.get(k, 0))
-    t = torch.from_numpy(buf)
+    t = torch.from_numpy(buf).to(dev)
     dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    buf = t.numpy()
+    buf = t.cpu().numpy()
     for i, k in enumerate(keys):
         out[k] = buf[i * n:(i + 1) * n].astype(np.uint64)
     for i, k in enumerate(SCALAR_KEYS):
@@ -68,8 +80,9 @@ def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, gro
         sizes = [world_range(theta, r, ws)[1] for r in range(ws)]
         pad = torch.zeros(max(sizes), dtype=torch.int64)
         pad[:cnt] = ws_local
+        pad = pad.to(dev)
         gathered = [torch.zeros_like(pad) for _ in range(ws)]
         dist.all_gather(gathered, pad, group=group)
         out["world_spread"] = np.concatenate(
-            [g.numpy()[:s] for g, s in zip(gathered, sizes)]).astype(np.uint32)
+            [g.cpu().numpy()[:s] for g, s in zip(gathered, sizes)]).astype(np.uint32)
     return out

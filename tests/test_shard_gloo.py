@@ -121,3 +121,15 @@ def test_sharded_gpu_sampling_two_ranks_one_gpu():
     q = ctx.SimpleQueue()
     mp.start_processes(_gpu_worker, args=(2, _free_port(), q), nprocs=2, join=True, start_method="spawn")
     assert q.get() == "ok"
+
+
+def test_collective_buffers_follow_the_backend(monkeypatch):
+    """Under NCCL the merge buffers go to the rank's CUDA device (NCCL moves device
+    memory only); under gloo they stay on the host."""
+    import torch
+    import torch.distributed as dist
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "nccl")
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 3)
+    assert shard.collective_device() == torch.device("cuda", 3)
+    monkeypatch.setattr(dist, "get_backend", lambda group=None: "gloo")
+    assert shard.collective_device() == torch.device("cpu")
