@@ -202,7 +202,8 @@ typedef struct imin_result {
 /* Influence Minimization (problem statement, Sec. 2.1): choose at most k
  * blockers from V \ S by Algorithm 1 (LSBM Algorithm 4, GSBM Sec. 5.2, LHGA
  * Sec. 5.3).  Stream tags: 0 spread estimate, 1/2 CP collections C1/C2,
- * 3/4 LRR collections L1/L2, 5/6/7 final estimates of B_L/B_U/B_R.
+ * 3/4 LRR collections L1/L2, 5 the final estimates of B_L, B_U and B_R (all
+ * three on the same worlds: Algorithm 1, line 4, with common random numbers).
  *   S, nS   host int32[nS], distinct, in [0, n), nS >= 1
  *   k       1 <= k < n - nS
  *   eps     in (0, 1); delta in (0, 1) (the paper uses delta = 1/n)

@@ -1112,7 +1112,12 @@ int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, do
         coll_free(&L1); coll_free(&L2);
     }
 
-    /* ---------------- Sandwich (Algorithm 1, lines 4-5) ---------------- */
+    /* ---------------- Sandwich (Algorithm 1, lines 4-5) ----------------
+     * Reading: the paper does not say which worlds the three (gamma, delta)-
+     * estimates draw.  They draw the same ones (stream tag 5, common random
+     * numbers): each candidate's estimate is still the stopping rule over an
+     * i.i.d. sequence of worlds, so each keeps its guarantee, and the argmin
+     * compares the candidates on paired worlds. */
     const int32_t *cand[3] = {BL, BU, BR};
     int32_t ncand[3] = {res->nBL, res->nBU, res->nBR};
     int use[3] = {do_L, do_U, do_R};
@@ -1122,7 +1127,7 @@ int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, do
         if (!use[c]) continue;
         double Ia = 0.0;
         res->n_final[c] = stop_rule(g, S, nS, cand[c], ncand[c], gamma, delta, key,
-                                    (uint32_t)(5 + c), inst, &Ia, NULL, NULL);
+                                    5u, inst, &Ia, NULL, NULL);
         res->I_after[c] = Ia;
         if (best < 0 || Ia < res->I_after[best]) best = c;
     }

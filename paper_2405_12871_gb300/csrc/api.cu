@@ -761,6 +761,234 @@ SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double b
 }
 
 // ---------------------------------------------------------------------------
+// Final estimates (Algorithm 1, line 4): the (gamma, delta)-estimates of the residual
+// spread of up to three candidate blocker sets, all on the worlds of stream tag 5.
+// One traversal per world serves every candidate (final_cta.cu); each candidate
+// stops at its own N, found exactly on the host from the per-world sizes.
+// ---------------------------------------------------------------------------
+constexpr uint32_t TAG_FINAL = 5u;
+
+struct FinalSpec {
+    const imin_graph *g;
+    const Query *q;        // the query (seeds)
+    const Query *qb[3];    // per candidate: S with the candidate's blockers (V'_s in G[V \ B])
+    bool use[3];
+    double gamma, delta;
+    uint64_t key;
+    uint32_t inst;
+    SpreadEst est[3];
+};
+
+struct FinalStats {
+    double kernel_ms = 0.0;
+    uint64_t launches = 0;
+};
+
+FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
+{
+    FinalStats fs;
+    const size_t ns = specs.size();
+    if (!ns) return fs;
+    int32_t nmax = 1;
+    for (const FinalSpec &f : specs) nmax = std::max(nmax, f.g->n);
+    const char *env = std::getenv("IMIN_FINAL_FUSED");
+    const bool fused = !(env && env[0] == '0') && nmax < (1 << 28);
+    if (!fused) {
+        // one reach-only stopping rule per candidate, each on the same worlds (tag 5):
+        // the same sizes as the fused traversal, so the same estimates
+        std::vector<StopSpec> sp;
+        std::vector<std::pair<size_t, int>> ref;
+        for (size_t i = 0; i < ns; ++i)
+            for (int c = 0; c < 3; ++c)
+                if (specs[i].use[c]) {
+                    sp.push_back(StopSpec{specs[i].g, specs[i].qb[c], specs[i].gamma, specs[i].delta,
+                                          specs[i].key, TAG_FINAL, specs[i].inst, SpreadEst{}});
+                    ref.emplace_back(i, c);
+                }
+        if (sp.empty()) return fs;
+        stop_rules(ctx, sp);
+        for (size_t k = 0; k < sp.size(); ++k) specs[ref[k].first].est[ref[k].second] = sp[k].est;
+        fs.kernel_ms = sp[0].est.kernel_ms;
+        fs.launches = sp[0].est.launches;
+        for (size_t k = 0; k < sp.size(); ++k) specs[ref[k].first].est[ref[k].second].kernel_ms = 0.0;
+        return fs;
+    }
+    for (size_t i = 0; i < ns; ++i)
+        autotune_reach(ctx, const_cast<imin_graph *>(specs[i].g), *specs[i].q);
+    // thresholds T_c = ceil(Upsilon1 W_c), W_c = |V'_s in G[V \ B_c]| + |S|
+    std::vector<std::array<double, 3>> W(ns), ups1(ns);
+    std::vector<std::array<unsigned long long, 3>> T(ns), sum(ns);
+    std::vector<std::array<uint64_t, 3>> N(ns);
+    std::vector<uint64_t> first(ns, 0), chunk(ns, 1);
+    for (size_t i = 0; i < ns; ++i) {
+        FinalSpec &f = specs[i];
+        uint64_t cmax = 1;
+        for (int c = 0; c < 3; ++c) {
+            sum[i][c] = 0;
+            N[i][c] = 0;
+            T[i][c] = 0;
+            if (!f.use[c]) continue;
+            W[i][c] = (double)f.qb[c]->nVs + (double)f.q->S.size();
+            const double ups = 4.0 * (IM_E - 2.0) * std::log(2.0 / f.delta) / (f.gamma * f.gamma);
+            ups1[i][c] = 1.0 + (1.0 + f.gamma) * ups;
+            const double Td = std::ceil(ups1[i][c] * W[i][c]);
+            if (!(Td < 1.8e19)) fail(IMIN_ERANGE, "stopping threshold too large");
+            T[i][c] = (unsigned long long)Td;
+            const uint64_t nm = (T[i][c] + f.q->S.size() - 1) / f.q->S.size();
+            if (nm >= ((uint64_t)1 << 32) - 1) fail(IMIN_ERANGE, "the stopping rule may need >= 2^32 worlds");
+            cmax = std::max(cmax, nm);
+        }
+        uint64_t c0 = (uint64_t)1 << 21;
+        if (const char *ce = std::getenv("IMIN_STOP_CHUNK")) {   // test hook: several chunks
+            const long long v = std::strtoll(ce, nullptr, 10);
+            if (v > 0) c0 = (uint64_t)v;
+        }
+        chunk[i] = std::min<uint64_t>(cmax, c0);
+    }
+    // launch shape: the graph's tuned CTA size (256 or 512 threads), as many CTAs as are
+    // resident, within half of the free memory
+    int bd = 256;
+    for (const FinalSpec &f : specs)
+        if (f.g->tuned_ctas > 0 && f.g->tuned_bd >= 512) bd = 512;
+    int minb = bd == 256 ? 8 : 4;
+    // tuning hook: IMIN_FINAL_SHAPE=<threads>:<CTAs per SM> (256 or 512 threads)
+    if (const char *fe = std::getenv("IMIN_FINAL_SHAPE")) {
+        int b = 0, m = 0;
+        if (std::sscanf(fe, "%d:%d", &b, &m) == 2 && (b == 256 || b == 512) && m >= 1) {
+            bd = b;
+            minb = std::min(m, b == 256 ? 8 : 4);
+        }
+    }
+    const int occ = std::max(1, std::min(minb, final_blocks_per_sm(bd)));
+    size_t off_q = 0;
+    const size_t per = final_slot_bytes(nmax, &off_q);
+    size_t freeb = 0, totalb = 0;
+    cudaMemGetInfo(&freeb, &totalb);
+    size_t avail = freeb / 2;
+    if (ctx->budget)
+        avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
+    size_t ctas = (size_t)ctx->num_sms * occ;
+    if (per * ctas > avail) ctas = std::max<size_t>(avail / per, 1);
+    if (per > freeb) fail(IMIN_ENOMEM, "not enough device memory for the final estimates");
+    DBuf ctl, cd, dtasks;
+    std::vector<DBuf> sizes(ns);
+    std::vector<std::vector<uint32_t>> hsz(ns);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    IM_CUDA(cudaEventCreate(&e0));
+    IM_CUDA(cudaEventCreate(&e1));
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } evg{e0, e1};
+    for (;;) {
+        std::vector<FTask> ht;
+        std::vector<size_t> idx;
+        for (size_t i = 0; i < ns; ++i) {
+            FinalSpec &f = specs[i];
+            uint32_t cands = 0;
+            for (int c = 0; c < 3; ++c)
+                if (f.use[c] && !N[i][c]) cands |= 1u << c;
+            if (!cands) continue;
+            const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
+            sizes[i].ensure(ctx, (size_t)cnt * 16 + 16);
+            FTask t{};
+            t.row_ptr = f.g->row_ptr.as<int32_t>();
+            t.ce = f.g->ce.as<uint4>();
+            t.S = f.q->dS.as<int32_t>();
+            t.nS = (int32_t)f.q->S.size();
+            t.cands = cands;
+            for (int c = 0; c < 3; ++c) {
+                t.B[c] = f.use[c] ? f.qb[c]->dB.as<int32_t>() : nullptr;
+                t.nB[c] = f.use[c] ? (int32_t)f.qb[c]->blocked.size() : 0;
+                t.stop_T[c] = ((cands >> c) & 1u) ? T[i][c] - sum[i][c] : 0ull;
+            }
+            t.key = f.key;
+            t.tag = TAG_FINAL;
+            t.inst = f.inst;
+            t.first = first[i];
+            t.count = (uint32_t)cnt;
+            t.sizes = sizes[i].as<uint32_t>();
+            ht.push_back(t);
+            idx.push_back(i);
+        }
+        if (ht.empty()) break;
+        const int nt = (int)ht.size();
+        ctl.ensure(ctx, (size_t)nt * 64);
+        cd.ensure(ctx, (size_t)nt * 8 + 16);
+        dtasks.ensure(ctx, (size_t)nt * sizeof(FTask));
+        for (int k = 0; k < nt; ++k) ht[k].acc = ctl.as<unsigned long long>() + (size_t)k * 8;
+        // the arena is prepared last (an allocation that does not fit drops the cached
+        // arenas); nibble maps must start clear, and every world leaves them clear
+        {
+            const size_t bytes = per * ctas;
+            const size_t key = per * 2654435761u + ctas;
+            const void *before = ctx->slots_final.p;
+            if (ctx->slots_final.p && ctx->slots_final.bytes < bytes) ctx->slots_final.release();
+            ctx->slots_final.ensure(ctx, bytes, false, true);
+            if (ctx->slots_final.p != before || ctx->slots_final_layout != key) {
+                IM_CUDA(cudaMemsetAsync(ctx->slots_final.p, 0, ctx->slots_final.bytes, ctx->stream));
+                ctx->slots_final_layout = key;
+            }
+        }
+        IM_CUDA(cudaMemsetAsync(ctl.p, 0, (size_t)nt * 64, ctx->stream));
+        IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)nt * 8, ctx->stream));
+        IM_CUDA(cudaMemcpyAsync(dtasks.p, ht.data(), ht.size() * sizeof(FTask), cudaMemcpyHostToDevice,
+                                ctx->stream));
+        IM_CUDA(cudaEventRecord(e0, ctx->stream));
+        launch_final_tasks(ctx, dtasks.as<FTask>(), nt, nmax, bd, (int)ctas, ctx->slots_final.p,
+                           cd.as<uint32_t>(), cd.as<uint32_t>() + nt);
+        IM_CUDA(cudaEventRecord(e1, ctx->stream));
+        IM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        IM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        fs.kernel_ms += ms;
+        fs.launches += 1;
+        std::vector<unsigned long long> acc((size_t)nt * 8);
+        std::vector<uint32_t> claims(nt);
+        IM_CUDA(cudaMemcpy(acc.data(), ctl.p, acc.size() * 8, cudaMemcpyDeviceToHost));
+        IM_CUDA(cudaMemcpy(claims.data(), cd.p, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < nt; ++k) {
+            const size_t i = idx[k];
+            FinalSpec &f = specs[i];
+            const uint64_t got = std::min<uint64_t>(claims[k], ht[k].count);
+            hsz[i].resize(got * 4);
+            if (got) IM_CUDA(cudaMemcpy(hsz[i].data(), sizes[i].p, got * 16, cudaMemcpyDeviceToHost));
+            // launch totals are shared by the candidates: the first served one gets them
+            int first_c = -1;
+            for (int c = 0; c < 3; ++c) {
+                if (!((ht[k].cands >> c) & 1u)) continue;
+                if (first_c < 0) first_c = c;
+                for (uint64_t j = 0; j < got; ++j) {
+                    sum[i][c] += hsz[i][j * 4 + c];
+                    if (sum[i][c] >= T[i][c]) {
+                        N[i][c] = first[i] + j + 1;
+                        break;
+                    }
+                }
+                if (!N[i][c] && got < ht[k].count) fail(IMIN_EDEVICE, "final estimate: threshold not reached");
+            }
+            SpreadEst &r = f.est[first_c];
+            r.nodes += acc[(size_t)k * 8 + 3];
+            r.edges += acc[(size_t)k * 8 + 4];
+            r.worlds += acc[(size_t)k * 8 + 5];
+            first[i] += got;
+            chunk[i] = std::min<uint64_t>(chunk[i] * 2, (uint64_t)1 << 30);
+        }
+    }
+    for (size_t i = 0; i < ns; ++i)
+        for (int c = 0; c < 3; ++c)
+            if (specs[i].use[c]) {
+                specs[i].est[c].N = N[i][c];
+                specs[i].est[c].I = W[i][c] * ups1[i][c] / (double)N[i][c];
+            }
+    return fs;
+}
+
+// ---------------------------------------------------------------------------
 // Collections: CP records (C1, C2) and LRR sets (L1, L2), appended together
 // ---------------------------------------------------------------------------
 bool store_tight()
@@ -1299,57 +1527,75 @@ struct Scheduler {
     {
         Timer t;
         std::vector<StopSpec> sp;
-        std::vector<std::pair<Inst *, int>> ref;   // candidate index, -1 = spread estimate
+        std::vector<Inst *> ihat;
+        std::vector<FinalSpec> fsp;
+        std::vector<Inst *> fin;
         for (Inst *I : active) {
             if (I->stage == ST_IHAT) {
                 sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
-                ref.emplace_back(I, -1);
+                ihat.push_back(I);
             } else if (I->stage == ST_FINAL) {
-                const bool use[3] = {I->do_L, I->do_U, I->do_R};
-                for (int c = 0; c < 3; ++c)
-                    if (use[c]) {
-                        sp.push_back(StopSpec{I->g, &I->qb[c], I->gamma, I->delta, I->key,
-                                              (uint32_t)(5 + c), I->inst, SpreadEst{}});
-                        ref.emplace_back(I, c);
-                    }
+                FinalSpec f{};
+                f.g = I->g;
+                f.q = &I->q;
+                for (int c = 0; c < 3; ++c) f.qb[c] = &I->qb[c];
+                f.use[0] = I->do_L;
+                f.use[1] = I->do_U;
+                f.use[2] = I->do_R;
+                f.gamma = I->gamma;
+                f.delta = I->delta;
+                f.key = I->key;
+                f.inst = I->inst;
+                fsp.push_back(f);
+                fin.push_back(I);
             }
         }
-        if (sp.empty()) return;
-        stop_rules(ctx, sp);
-        kms[0] += sp[0].est.kernel_ms;
-        reach_launches += sp[0].est.launches;
-        bool any_ihat = false, any_final = false;
+        if (sp.empty() && fsp.empty()) return;
+        Timer t_ihat;
+        if (!sp.empty()) {
+            stop_rules(ctx, sp);
+            kms[0] += sp[0].est.kernel_ms;
+            reach_launches += sp[0].est.launches;
+        }
+        const double dt_ihat = t_ihat.ms();
+        Timer t_fin;
+        if (!fsp.empty()) {
+            const FinalStats st = final_estimates(ctx, fsp);
+            kms[0] += st.kernel_ms;
+            reach_launches += st.launches;
+        }
+        const double dt_fin = t_fin.ms();
         for (size_t i = 0; i < sp.size(); ++i) {
-            Inst &I = *ref[i].first;
-            const int c = ref[i].second;
+            Inst &I = *ihat[i];
             const SpreadEst &e = sp[i].est;
             imin_result *res = I.res;
             res->worlds_sampled += e.worlds;
             res->edges_scanned += e.edges;
             res->reach_nodes += e.nodes;
             res->reach_edges += e.edges;
-            if (c < 0) {
-                I.I_hat = e.I;
-                res->I_hat = e.I;
-                res->n_spread = e.N;
-                any_ihat = true;
-            } else {
+            I.I_hat = e.I;
+            res->I_hat = e.I;
+            res->n_spread = e.N;
+        }
+        for (size_t i = 0; i < fsp.size(); ++i) {
+            Inst &I = *fin[i];
+            imin_result *res = I.res;
+            for (int c = 0; c < 3; ++c) {
+                if (!fsp[i].use[c]) continue;
+                const SpreadEst &e = fsp[i].est[c];
+                res->worlds_sampled += e.worlds;
+                res->edges_scanned += e.edges;
+                res->reach_nodes += e.nodes;
+                res->reach_edges += e.edges;
                 res->I_after[c] = e.I;
                 res->n_final[c] = e.N;
-                any_final = true;
             }
         }
-        for (size_t i = 0; i < sp.size(); ++i) {
-            Inst &I = *ref[i].first;
-            if (ref[i].second < 0)
-                next_after(I, -1);
-            else if (I.stage == ST_FINAL)
-                finish(I);
-        }
-        const double dt = t.ms();
-        if (any_ihat && !any_final) ms[0] += dt;
-        else if (any_final && !any_ihat) ms[5] += dt;
-        else { ms[0] += dt / 2; ms[5] += dt / 2; }
+        for (Inst *I : ihat) next_after(*I, -1);
+        for (Inst *I : fin) finish(*I);
+        const double rest = t.ms() - dt_ihat - dt_fin;
+        ms[0] += dt_ihat + (fsp.empty() ? rest : 0.0);
+        ms[5] += dt_fin + (fsp.empty() ? 0.0 : rest);
     }
 
     // one doubling round of LSBM (upper = false) or GSBM (upper = true)
@@ -1586,6 +1832,7 @@ void imin_destroy(imin_ctx *ctx)
     ctx->slots.release();
     ctx->slots_lower.release();
     ctx->big_slots.release();
+    ctx->slots_final.release();
     ctx->misc.release();
     delete ctx;
 }

@@ -109,7 +109,8 @@ struct imin_ctx {
     DBuf slots;             // world-kernel slot arena (reach-only and upper-bound worlds)
     DBuf slots_lower;       // slot arena of lower-bound worlds (larger slots, fewer of them)
     DBuf big_slots;         // slots for deferred (oversized) worlds
-    size_t slots_layout = 0, slots_lower_layout = 0, big_slots_layout = 0;
+    DBuf slots_final;       // slots of the fused final estimates
+    size_t slots_layout = 0, slots_lower_layout = 0, big_slots_layout = 0, slots_final_layout = 0;
     // L2 persistence for the graph's edge array (0 = not available)
     size_t l2_window_bytes = 0, l2_persist_bytes = 0;
     size_t prev_persist_limit = 0;
@@ -235,6 +236,29 @@ struct WTask {
 
 WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t count,
                 const uint32_t *list, const WorldOut &out);
+
+// Final estimates of up to three candidate blocker sets on shared worlds (final_cta.cu):
+// one traversal per world, a 4-bit field of candidate bits per node.
+struct FTask {
+    const int32_t *row_ptr;
+    const uint4 *ce;
+    const int32_t *S;                // device, nS seeds
+    int32_t nS;
+    uint32_t cands;                  // candidates served (bits 0..2)
+    const int32_t *B[3];             // device blocked lists per candidate
+    int32_t nB[3];
+    uint64_t key;
+    uint32_t tag, inst;
+    uint64_t first;
+    uint32_t count;
+    unsigned long long stop_T[3];    // per candidate: sizes still missing to its threshold
+    unsigned long long *acc;         // [0..2] running sizes, [3] queue entries, [4] edges, [5] worlds
+    uint32_t *sizes;                 // [count][4]: |R_j| per candidate (0 where not served)
+};
+size_t final_slot_bytes(int32_t n, size_t *off_queue);
+int final_blocks_per_sm(int bd);
+void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int bd, int ctas,
+                        void *slot_base, uint32_t *d_claim, uint32_t *d_done);
 
 // CTA-per-world reach kernel (reach_cta.cuh, sampler_cta.cu): the compiled shapes
 // {threads per CTA, CTAs per SM}

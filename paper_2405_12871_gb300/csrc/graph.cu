@@ -22,12 +22,12 @@ unsigned long long g_kernel_launches = 0;
 static bool trim_slot_arenas(imin_ctx *ctx)
 {
     bool any = false;
-    for (DBuf *b : {&ctx->slots, &ctx->slots_lower, &ctx->big_slots})
+    for (DBuf *b : {&ctx->slots, &ctx->slots_lower, &ctx->big_slots, &ctx->slots_final})
         if (b->p) {
             b->release();
             any = true;
         }
-    ctx->slots_layout = ctx->slots_lower_layout = ctx->big_slots_layout = 0;
+    ctx->slots_layout = ctx->slots_lower_layout = ctx->big_slots_layout = ctx->slots_final_layout = 0;
     return any;
 }
 

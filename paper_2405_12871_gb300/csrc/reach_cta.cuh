@@ -285,6 +285,54 @@ __device__ __forceinline__ void pass(const Op &op, const Rec &rec, bool act, int
     __syncwarp();
 }
 
+// The same pass for traversals that record nothing besides the queue (reach-only and
+// LRR worlds): each lane claims its own live targets directly, up to four independent
+// atomics in flight per lane (no staging, one round trip to the bitmap), and the new
+// nodes are appended at offsets taken from four ballots.  The queue order differs from
+// the staged pass; a world's results are sets and do not depend on it.
+template <class Op>
+__device__ __forceinline__ void pass_direct(const Op &op, bool act, int it, int ob, int oe, const Coins &K,
+                                            uint32_t *bm, int32_t *Q, int *app, int tail, int lane,
+                                            uint32_t lt_mask)
+{
+    uint32_t live = 0;
+    int4 c4 = make_int4(0, 0, 0, 0);
+    if (act) live = op.live(it, ob, oe, K, c4);
+    uint32_t o0 = ~0u, o1 = ~0u, o2 = ~0u, o3 = ~0u;
+    const uint32_t m0 = 1u << (c4.x & 31), m1 = 1u << (c4.y & 31), m2 = 1u << (c4.z & 31),
+                   m3 = 1u << (c4.w & 31);
+    if (live & 1u) o0 = atomicOr(&bm[c4.x >> 5], m0);
+    if (live & 2u) o1 = atomicOr(&bm[c4.y >> 5], m1);
+    if (live & 4u) o2 = atomicOr(&bm[c4.z >> 5], m2);
+    if (live & 8u) o3 = atomicOr(&bm[c4.w >> 5], m3);
+    const bool f0 = !(o0 & m0), f1 = !(o1 & m1), f2 = !(o2 & m2), f3 = !(o3 & m3);
+    const uint32_t b0 = __ballot_sync(IMIN_FULL, f0), b1 = __ballot_sync(IMIN_FULL, f1),
+                   b2 = __ballot_sync(IMIN_FULL, f2), b3 = __ballot_sync(IMIN_FULL, f3);
+    const int tot = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
+    if (tot == 0) return;
+    int base = 0;
+    if (lane == 0) base = atomicAdd(app, tot);
+    base = __shfl_sync(IMIN_FULL, base, 0);
+    int pos = tail + base + __popc(b0 & lt_mask) + __popc(b1 & lt_mask) + __popc(b2 & lt_mask) +
+              __popc(b3 & lt_mask);
+    if (f0) Q[pos++] = c4.x;
+    if (f1) Q[pos++] = c4.y;
+    if (f2) Q[pos++] = c4.z;
+    if (f3) Q[pos] = c4.w;
+}
+
+template <class Op, class Rec>
+__device__ __forceinline__ void pass_any(const Op &op, const Rec &rec, bool act, int it, int ob, int oe, int src,
+                                         int level, const Coins &K, uint32_t *bm, int32_t *Q, int *cand,
+                                         int *cand2, int *app, int *npairs, int tail, int lane,
+                                         uint32_t lt_mask)
+{
+    if constexpr (Rec::kOn)
+        pass(op, rec, act, it, ob, oe, src, level, K, bm, Q, cand, cand2, app, npairs, tail, lane, lt_mask);
+    else
+        pass_direct(op, act, it, ob, oe, K, bm, Q, app, tail, lane, lt_mask);
+}
+
 // Breadth-first expansion of Q[0, tail0) until no level adds a node; returns the
 // final tail.  The caller zeroes the counters of both parities and passes a CTA
 // barrier before the call; the call ends with a CTA barrier.
@@ -303,17 +351,25 @@ __device__ __forceinline__ int bfs(const Op &op, const Rec &rec, const Coins &K,
             sh.slice[p ^ 1] = sh.nbig[p ^ 1] = sh.piece[p ^ 1] = 0;
             rec.level_start(lvl, head);
         }
-        // ---- phase 1: 32-node slices, one warp each ----
+        // ---- phase 1: 32-node slices, one warp each; the queue entries of the next
+        // slice are read while the current one is expanded ----
+        int sl = 0;
+        if (lane == 0) sl = atomicAdd(&sh.slice[p], 1);
+        sl = __shfl_sync(IMIN_FULL, sl, 0);
+        int nbase = head + sl * 32;
+        int nu = nbase + lane < tail ? Q[nbase + lane] : 0;
         for (;;) {
-            int sl = 0;
-            if (lane == 0) sl = atomicAdd(&sh.slice[p], 1);
-            sl = __shfl_sync(IMIN_FULL, sl, 0);
-            const int base = head + sl * 32;
+            const int base = nbase;
             if (base >= tail) break;
             const int i = base + lane;
+            const int u = nu;
+            if (lane == 0) sl = atomicAdd(&sh.slice[p], 1);
+            sl = __shfl_sync(IMIN_FULL, sl, 0);
+            nbase = head + sl * 32;
+            nu = nbase + lane < tail ? Q[nbase + lane] : 0;
             int b = 0, e = 0, cnt = 0;
             if (i < tail) {
-                op.range(Q[i], b, e);
+                op.range(u, b, e);
                 cnt = Op::count(b, e);
                 if (Op::kCountEdges) wedges += (unsigned long long)(e - b);
             }
@@ -351,7 +407,7 @@ __device__ __forceinline__ int bfs(const Op &op, const Rec &rec, const Coins &K,
                 const int ob = __shfl_sync(IMIN_FULL, b, pos);
                 const int oe = __shfl_sync(IMIN_FULL, e, pos);
                 const int ox = __shfl_sync(IMIN_FULL, excl, pos);
-                pass(op, rec, t < total, Op::first(ob) + (t - ox), ob, oe, base + pos, lvl, K, bm, Q, cand,
+                pass_any(op, rec, t < total, Op::first(ob) + (t - ox), ob, oe, base + pos, lvl, K, bm, Q, cand,
                      cand2, &sh.app[p], &sh.npairs, tail, lane, lt_mask);
             }
         }
@@ -393,7 +449,7 @@ __device__ __forceinline__ int bfs(const Op &op, const Rec &rec, const Coins &K,
                 const int i0 = Op::first(ob) + (pc - sh.pp[lo]) * PIECE;
                 const int iend = min(i0 + PIECE, Op::first(ob) + Op::count(ob, oe));
                 for (int is = i0; is < iend; is += 32)
-                    pass(op, rec, is + lane < iend, is + lane, ob, oe, oi, lvl, K, bm, Q, cand, cand2, &sh.app[p],
+                    pass_any(op, rec, is + lane < iend, is + lane, ob, oe, oi, lvl, K, bm, Q, cand, cand2, &sh.app[p],
                          &sh.npairs, tail, lane, lt_mask);
             }
         }

@@ -193,3 +193,25 @@ def test_controller_pin_graphs(ctx, which):
         kw = dict(kw, eps=0.2, delta=0.05)
         compare(G.solve(S, **kw), og.solve(S, **kw))
     G.free()
+
+
+@pytest.mark.parametrize("chunk", [None, "613"])
+def test_final_estimates_fused_and_separate(ctx, monkeypatch, chunk):
+    """The final estimates of the three candidates run as one traversal per world with a
+    per-node candidate mask; one stopping rule per candidate on the same worlds gives
+    the same N and estimates, and both equal the oracle's (also in many small chunks)."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=7)
+    S = synth.seeds_top_outdeg(g, 12, 0.01, seed=8)
+    og = oracle.OracleGraph.from_graph(g)
+    kw = dict(k=15, eps=0.3, delta=1.0 / g.n, key=4)
+    if chunk:
+        monkeypatch.setenv("IMIN_STOP_CHUNK", chunk)
+    G = ctx.load_graph(g)
+    fused = G.solve(S, **kw)
+    monkeypatch.setenv("IMIN_FINAL_FUSED", "0")
+    separate = G.solve(S, **kw)
+    G.free()
+    monkeypatch.delenv("IMIN_FINAL_FUSED")
+    compare(fused, separate)
+    compare(fused, og.solve(S, **kw))
+    assert len(set(fused["n_final"])) > 1      # each candidate stops at its own N
