@@ -103,29 +103,19 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def cpu_oracle_projection(g, S, cfg, counts, budget_s=12.0, seed_tag=11):
-    """Time the oracle (as it stands, single-threaded) on a bounded sample of the
-    workload's worlds and project the solve time from the solve's own world counts:
-    reach-only worlds (spread estimates), CP worlds (LSBM), LRR worlds (GSBM)."""
+def cpu_oracle_projection(g, S, cfg, counts, worlds=(1000, 500, 300), seed_tag=11):
+    """Time the oracle (as it stands, single-threaded) on a fixed sample of the workload's
+    worlds per sampling mode and project the solve time from the solve's own world
+    counts: reach-only worlds (spread estimates), CP worlds (LSBM), LRR worlds (GSBM)."""
     import oracle
     og = oracle.OracleGraph.from_graph(g)
     per = {}
-    samples = {"reach": (1, counts["reach_worlds"]), "lower": (2, counts["cp_worlds"]),
-               "upper": (4, counts["lrr_worlds"])}
-    share = {"reach": 0.5, "lower": 0.3, "upper": 0.2}
     desc = []
-    for name, (mode, _) in samples.items():
-        t_budget = budget_s * share[name]
-        done, t = 0, 0.0
-        batch = 2
-        while t < t_budget and done < 100_000:
-            t0 = time.perf_counter()
-            og.sample(S, theta=batch, first=1_000_000 + done, key=7, tag=seed_tag, mode=mode)
-            t += time.perf_counter() - t0
-            done += batch
-            batch = min(batch * 2, 64)
-        per[name] = t / max(done, 1)
-        desc.append(f"{done} {name} worlds")
+    for (name, mode), nw in zip((("reach", 1), ("lower", 2), ("upper", 4)), worlds):
+        t0 = time.perf_counter()
+        og.sample(S, theta=nw, first=1_000_000, key=7, tag=seed_tag, mode=mode)
+        per[name] = (time.perf_counter() - t0) / nw
+        desc.append(f"{nw} {name} worlds")
     proj = (per["reach"] * counts["reach_worlds"] + per["lower"] * counts["cp_worlds"] +
             per["upper"] * counts["lrr_worlds"])
     sample = ("oracle (single-threaded C, as committed) timed on " + ", ".join(desc) +
@@ -154,30 +144,52 @@ def _oracle_task(job):
     return theta
 
 
-def cpu_oracle_parallel(g, S, counts, procs=None, per_worker=(48, 24, 24), seed_tag=12):
+class OraclePool:
     """The same oracle, unchanged, with its world loop split over every host core: each
-    worker samples its own range of worlds (worlds are index-addressed, so the ranges
-    are independent).  Per mode, the wall time of `procs` x n worlds gives a rate; the
-    solve time is projected from the solve's world counts as in the one-core line."""
-    import multiprocessing as mp
-    procs = procs or os.cpu_count() or 1
-    ctxp = mp.get_context("spawn")        # never fork a process that holds a CUDA context
-    with ctxp.Pool(procs, initializer=_oracle_init,
-                   initargs=(g.n, g.row_ptr, g.col, g.prob, np.asarray(S, np.int32))) as pool:
-        pool.map(_oracle_task, [(1, 5_000_000 + 2 * i, 2, seed_tag) for i in range(procs)])   # warm
+    worker process holds its own copy of the graph and samples its own world range
+    (worlds are index-addressed, so the ranges are independent)."""
+
+    def __init__(self, g, S, procs=None):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        ctxp = mp.get_context("spawn")        # never fork a process that holds a CUDA context
+        self.pool = ctxp.Pool(self.procs, initializer=_oracle_init,
+                              initargs=(g.n, g.row_ptr, g.col, g.prob, np.asarray(S, np.int32)))
+        self.pool.map(_oracle_task, [(1, 5_000_000 + 2 * i, 2, 3) for i in range(self.procs)])   # warm
+
+    def rates(self, worlds, seed_tag, first=2_000_000):
+        """worlds per mode (reach, lower, upper), split evenly over the processes;
+        returns wall-clock worlds per second per mode."""
         rates = {}
-        for name, mode, nw in (("reach", 1, per_worker[0]), ("lower", 2, per_worker[1]),
-                               ("upper", 4, per_worker[2])):
-            jobs = [(mode, 2_000_000 + i * nw, nw, seed_tag) for i in range(procs)]
+        for (name, mode), total in zip((("reach", 1), ("lower", 2), ("upper", 4)), worlds):
+            per = max(1, -(-int(total) // self.procs))
+            jobs = [(mode, first + i * per, per, seed_tag) for i in range(self.procs)]
             t0 = time.perf_counter()
-            done = sum(pool.map(_oracle_task, jobs))
+            done = sum(self.pool.map(_oracle_task, jobs))
             rates[name] = done / (time.perf_counter() - t0)
-    proj = (counts["reach_worlds"] / rates["reach"] + counts["cp_worlds"] / rates["lower"] +
+        return rates
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def project(counts, rates):
+    return (counts["reach_worlds"] / rates["reach"] + counts["cp_worlds"] / rates["lower"] +
             counts["lrr_worlds"] / rates["upper"])
-    sample = (f"the oracle's world loop split over {procs} processes, each on its own world range: "
-              f"{procs} x ({per_worker[0]} reach, {per_worker[1]} lower, {per_worker[2]} upper) worlds, "
-              "wall-clock rates per mode; solve time projected from the solve's world counts")
-    return proj, sample, procs
+
+
+def cpu_oracle_parallel(g, S, counts, worlds=(10_000, 10_000, 10_000), seed_tag=12):
+    pool = OraclePool(g, S)
+    try:
+        rates = pool.rates(worlds, seed_tag)
+    finally:
+        pool.close()
+    sample = (f"the oracle's world loop split over {pool.procs} processes, each on its own world range: "
+              f"{worlds[0]} reach, {worlds[1]} lower and {worlds[2]} upper worlds in all, wall-clock rates "
+              "per mode; solve time projected from the solve's world counts; greedy and host math not "
+              "included")
+    return project(counts, rates), sample, pool.procs
 
 
 def solve_counts(r):
@@ -192,26 +204,34 @@ def run_reference(args, rank, world):
         return 0
     from paper_2405_12871_gb300 import synth
     g, S, cfg = synth.workload_cl1m()
-    # world counts of the solve: fixed from the paper's formulas on this workload are not
-    # known without running it, so the reference arm uses representative counts measured
-    # by the GPU arm (committed in profiles/) when present, else a nominal mix
+    # the solve's world counts are not known without running it: the reference arm uses
+    # the counts the GPU arm measured (committed in profiles/) when present
     counts = {"reach_worlds": 900_000, "cp_worlds": 12_000, "lrr_worlds": 200_000}
     pth = os.path.join(ROOT, "profiles", "solve_counts_cl1m.json")
     if os.path.exists(pth):
         counts = json.load(open(pth))
+    pool = OraclePool(g, S)
+    per_step = (1600, 800, 640)
     vals = []
-    sample = ""
-    for step in range(args.warmup + args.steps):
-        proj, sample, _ = cpu_oracle_projection(g, S, cfg, counts, budget_s=6.0,
-                                                seed_tag=20 + step)
-        if step >= args.warmup:
-            vals.append(proj)
+    try:
+        for step in range(args.warmup + args.steps):
+            v = project(counts, pool.rates(per_step, seed_tag=20 + step, first=3_000_000 + step * 10_000))
+            if step >= args.warmup:
+                vals.append(v)
+    finally:
+        pool.close()
     v = float(np.mean(vals))
+    sample = (f"oracle (C, as committed) with its world loop split over {pool.procs} host processes; each "
+              f"step times {per_step[0]} reach, {per_step[1]} lower and {per_step[2]} upper worlds of the "
+              f"CL-1M workload and projects the solve time from the solve's world counts "
+              f"(reach {counts['reach_worlds']}, CP {counts['cp_worlds']}, LRR {counts['lrr_worlds']}); "
+              "greedy and host math not included")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-            "data": "synthetic", "config": WORKLOAD,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "data": "synthetic", "config": dict(WORKLOAD, parallelism=f"replicas x{world}"),
+            "projected": True,
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -399,6 +419,64 @@ def run_serve(args):
 
 
 # ---------------------------------------------------------------------------
+def run_rmat(args):
+    """The R-MAT-4M configuration (4,194,304 nodes, 2^26 edge draws, trivalency p,
+    |S| = 100 uniform seeds, k = 200, eps = 0.1, delta = 1/n): reach-only sampling
+    throughput with its roofline (a world reaches about half a million nodes, so the
+    graph and the visited maps do not fit in L2), then timed solves."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    t0 = time.time()
+    g, S, cfg = synth.workload_rmat4m()
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    ctx = _lib.Context(0, stream=stream.cuda_stream)
+    G = ctx.load_graph(g)
+    pk = peaks()
+    peak = float(pk.get("hbm_gbs", 6800.0))
+    out = {"mode": "rmat", "config": {"workload": "rmat-4M", "nodes": g.n, "edges": g.m, "a_b_c": [0.57, 0.19, 0.19],
+                                      "p": "uniform from {0.1, 0.01, 0.001}", "seeds": 100, "k": cfg["k"],
+                                      "eps": cfg["eps"], "delta": "1/n"}, "graph_gen_s": round(gen_s, 1)}
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    theta = args.rmat_worlds
+    G.sample(S, theta=64, key=0, tag=0, first=10_000_000, mode=0)
+    ev0.record(stream)
+    r = G.sample(S, theta=theta, key=0, tag=0, first=0, mode=0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    alg = 16.0 * r["total_spread"] + 8.0 * r["edges_scanned"]
+    out["reach_sampling"] = {"worlds": theta, "s": dt, "samples_per_s": theta / dt,
+                             "gteps": r["edges_scanned"] / dt / 1e9, "nodes_per_world": r["total_spread"] / theta,
+                             "edges_per_world": r["edges_scanned"] / theta,
+                             "roofline": {"bound": "hbm", "achieved": alg / dt / 1e9, "peak": peak, "unit": "GB/s",
+                                          "frac": alg / dt / 1e9 / peak, "kernel": "cta_world_kernel<reach-only>",
+                                          "launch_shape": G.tuning(),
+                                          "algorithmic_bytes": "16 B per reached node + 8 B per scanned edge"}}
+    print(json.dumps(out), flush=True)
+    if args.rmat_solves:
+        kw = dict(k=cfg["k"], eps=cfg["eps"], delta=cfg["delta"], key=cfg["key"])
+        sol = []
+        for i in range(args.rmat_solves):
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            rs = G.solve(S, **kw)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            sol.append({"s": ev0.elapsed_time(ev1) / 1e3, "stage_ms": [round(x, 1) for x in rs["ms_stage"]],
+                        "kernel_ms": [round(x, 1) for x in rs["kernel_ms"]],
+                        "final_kernel_ms": round(rs["final_kernel_ms"], 1), "worlds": int(rs["worlds_sampled"]),
+                        "edges": int(rs["edges_scanned"]), "I_hat": rs["I_hat"], "I_after": rs["I_after"],
+                        "chosen": rs["chosen"], "counts": solve_counts(rs)})
+        out["solves"] = sol
+        print(json.dumps(out), flush=True)
+    G.free()
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -407,6 +485,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mc-check", action="store_true")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched vs plain: the first N instances of the 512-instance Chung-Lu "
                          "batch recipe, solved one by one and as one imin_solve_batch")
@@ -423,6 +502,10 @@ def main():
                     help="worlds per AG / GR estimate")
     ap.add_argument("--baseline-eval", type=int, default=100_000,
                     help="worlds of the final spread re-estimate")
+    ap.add_argument("--rmat", action="store_true",
+                    help="the R-MAT-4M configuration: reach-only sampling roofline and timed solves")
+    ap.add_argument("--rmat-worlds", type=int, default=2000)
+    ap.add_argument("--rmat-solves", type=int, default=1)
     ap.add_argument("--reach-only-worlds", type=int, default=0,
                     help="profiling case: run two imin_sample launches of this many reach-only "
                          "worlds on the same workload (the stopping rule's kernel) and exit")
@@ -440,6 +523,8 @@ def main():
         return run_baselines(args)
     if args.sweep:
         return run_sweep(args)
+    if args.rmat:
+        return run_rmat(args)
 
     import torch
     import torch.distributed as dist
@@ -502,6 +587,21 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         step_s = float(t.item())
 
+    # ---- independent Monte Carlo re-estimate of the chosen blockers' spread ----
+    mc = None
+    if rank == 0 and not args.no_mc_check:
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        ev = G.sample(S, results[-1]["blockers"], theta=1_000_000, key=1, tag=9, mode=0, per_world=True)
+        torch.cuda.synchronize()
+        ws = ev["world_spread"].astype(np.float64)
+        m = float(ws.mean())
+        est = float(results[-1]["I_after"][results[-1]["chosen"]])
+        mc = {"worlds": 1_000_000, "stream": "key 1, tag 9 (no solve draws it)", "estimate": est, "mc_mean": m,
+              "rel_diff": abs(est - m) / m, "mc_rel_stderr": float(ws.std(ddof=1) / np.sqrt(len(ws)) / m),
+              "tolerance": 0.01, "within_tolerance": abs(est - m) / m <= 0.01,
+              "seconds": time.perf_counter() - a}
+
     # ---- end to end: upload the graph from host buffers, solve, read back, free ----
     e2e = None
     if not args.no_e2e:
@@ -537,38 +637,77 @@ def main():
                if pinned else "pageable"}
         assert list(r2["blockers"]) == list(results[-1]["blockers"])
 
-    # ---- throughput and roofline of the dominant kernel (reach-only world kernel) ----
+    # ---- throughput and roofline of the two stopping-rule kernels ----
     rr = results[-1]
     worlds = np.mean([x["worlds_sampled"] for x in results])
     edges = np.mean([x["edges_scanned"] for x in results])
-    kms = np.mean([x["kernel_ms"][0] for x in results]) / 1e3
-    nodes = np.mean([x["reach_nodes"] for x in results])
-    redges = np.mean([x["reach_edges"] for x in results])
-    launches = np.mean([x["reach_launches"] for x in results])
-    alg_bytes = 16.0 * nodes + 8.0 * redges          # per solve, all reach launches
     pk = peaks()
     peak = float(pk.get("hbm_gbs", 6800.0))
-    achieved = alg_bytes / kms / 1e9 if kms > 0 else 0.0
-    # DRAM traffic per launch: bytes per algorithmic byte from one ncu capture of the
-    # same kernel and launch shape on a smaller reach-only case, times this launch's
-    # algorithmic bytes (traffic grows with the nodes and edges a launch processes)
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "reach_kernel_traffic.json")
-    if os.path.exists(tp):
-        try:
-            tj = json.load(open(tp))
-            if tj.get("shape") == shape:
-                traffic = tj["dram_bytes_per_alg_byte"] * alg_bytes / max(launches, 1)
-        except Exception:
-            traffic = None
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "kernel": "cta_world_kernel<reach-only, stopping rule>",
-            "launch_shape": shape,
-            "per_launch_ms": kms * 1e3 / max(launches, 1),
-            "algorithmic_bytes": "16 B per reached node + 8 B per scanned edge",
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk
-            else "fallback 6.8 TB/s"}
+    peak_src = ("MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback 6.8 TB/s")
+
+    def roofline(kms, nodes, redges, launches, kernel, shape, traffic_file):
+        alg_bytes = 16.0 * nodes + 8.0 * redges
+        achieved = alg_bytes / kms / 1e9 if kms > 0 else 0.0
+        # DRAM traffic per launch: bytes per algorithmic byte from one ncu capture of the
+        # same kernel and launch shape on a smaller case, times this launch's algorithmic
+        # bytes (traffic grows with the nodes and edges a launch processes)
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", traffic_file)
+        if os.path.exists(tp):
+            try:
+                tj = json.load(open(tp))
+                if tj.get("shape") == shape:
+                    traffic = tj["dram_bytes_per_alg_byte"] * alg_bytes / max(launches, 1)
+            except Exception:
+                traffic = None
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "launch_shape": shape,
+                "per_launch_ms": kms * 1e3 / max(launches, 1), "launches_per_solve": launches,
+                "algorithmic_bytes": "16 B per queue entry (row_ptr pair, queue write + read, visited "
+                                     "word) + 8 B per scanned edge",
+                "peak_source": peak_src}
+
+    f_kms = np.mean([x["final_kernel_ms"] for x in results]) / 1e3
+    f_nodes = np.mean([x["final_entries"] for x in results])
+    f_edges = np.mean([x["final_edges"] for x in results])
+    f_launch = np.mean([x["final_launches"] for x in results])
+    r_kms = np.mean([x["kernel_ms"][0] for x in results]) / 1e3 - f_kms
+    r_nodes = np.mean([x["reach_nodes"] for x in results]) - f_nodes
+    r_edges = np.mean([x["reach_edges"] for x in results]) - f_edges
+    r_launch = np.mean([x["reach_launches"] for x in results]) - f_launch
+    fshape = {"threads": 512 if shape.get("threads", 256) >= 512 else 256,
+              "ctas_per_sm": 4 if shape.get("threads", 256) >= 512 else 8, "map": "4-bit candidate field per node"}
+    roof_final = roofline(f_kms, f_nodes, f_edges, f_launch,
+                          "cta_final_kernel (the three final estimates in one traversal per world)", fshape,
+                          "final_kernel_traffic.json")
+    roof_reach = roofline(r_kms, r_nodes, r_edges, r_launch,
+                          "cta_world_kernel<reach-only, stopping rule> (the spread estimate I_hat)", shape,
+                          "reach_kernel_traffic.json")
+    # the roofline reported is that of the kernel with the larger device time
+    roof, roof_other = (roof_final, roof_reach) if f_kms >= r_kms else (roof_reach, roof_final)
+
+    # ---- the parity configuration: one full GPU solve next to one full oracle solve ----
+    er = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        ge, Se, ce = synth.workload_er1k()
+        Ge = ctx.load_graph(ge)
+        kwe = dict(k=ce["k"], eps=0.2, delta=1.0 / ge.n, key=ce["key"])
+        Ge.solve(Se, **kwe)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        re_ = Ge.solve(Se, **kwe)
+        torch.cuda.synchronize()
+        t_gpu = time.perf_counter() - a
+        Ge.free()
+        a = time.perf_counter()
+        ro = oracle.OracleGraph.from_graph(ge).solve(Se, **kwe)
+        t_or = time.perf_counter() - a
+        er = {"workload": "erdos-renyi-1K (1,000 nodes, 5,000 edges, |S| = 10, k = 5, eps = 0.2, delta = 1/n)",
+              "gpu_s": t_gpu, "oracle_s": t_or, "oracle_cores": 1, "projected": False,
+              "identical": list(re_["blockers"]) == list(ro["blockers"]) and re_["I_after"] == ro["I_after"],
+              "worlds": int(re_["n_spread"] + sum(re_["n_final"]) + re_["theta_C1"] + re_["theta_C2"] +
+                            re_["theta_L1"] + re_["theta_L2"])}
 
     line = {"metric": METRIC, "value": step_s, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": False,
@@ -578,11 +717,16 @@ def main():
             "solves_per_s": world / step_s,
             "stage_ms": [round(x, 2) for x in rr["ms_stage"]],
             "kernel_ms": [round(x, 2) for x in rr["kernel_ms"]],
+            "final_kernel_ms": round(rr["final_kernel_ms"], 2),
             "counts": solve_counts(rr), "I_hat": rr["I_hat"], "I_after": rr["I_after"],
             "chosen": rr["chosen"], "gpu_launches": int(np.mean([x["kernel_launches"] for x in results])),
-            "roofline": roof, "clocks": clk, "graph_gen_s": round(gen_s, 1)}
+            "roofline": roof, "roofline_other": roof_other, "clocks": clk, "graph_gen_s": round(gen_s, 1)}
     if e2e:
         line["e2e"] = e2e
+    if mc:
+        line["mc_check"] = mc
+    if er:
+        line["er1k_full_solve"] = er
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         proj, sample, _ = cpu_oracle_projection(g, S, cfg, solve_counts(rr))
         line["cpu_baseline"] = {"value": proj, "unit": UNIT, "cores": 1, "kind": "oracle",

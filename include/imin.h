@@ -197,6 +197,11 @@ typedef struct imin_result {
     uint64_t reach_edges;   /* edges scanned by the reach-only launches */
     uint64_t reach_launches;/* reach-only world-kernel launches */
     uint64_t kernel_launches; /* kernels the library launched during the call */
+    double final_kernel_ms; /* device time of the fused final-estimate launches (part of kernel_ms[0]) */
+    uint64_t final_entries; /* queue entries of those launches: nodes reached, one entry per new
+                               candidate set (part of reach_nodes) */
+    uint64_t final_edges;   /* edges they scanned (part of reach_edges) */
+    uint64_t final_launches;/* fused final-estimate launches (part of reach_launches) */
 } imin_result;
 
 /* Influence Minimization (problem statement, Sec. 2.1): choose at most k

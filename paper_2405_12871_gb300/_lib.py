@@ -59,6 +59,8 @@ class Result(C.Structure):
         ("worlds_sampled", C.c_uint64), ("ms_stage", C.c_double * 8),
         ("kernel_ms", C.c_double * 4), ("reach_nodes", C.c_uint64), ("reach_edges", C.c_uint64),
         ("reach_launches", C.c_uint64), ("kernel_launches", C.c_uint64),
+        ("final_kernel_ms", C.c_double), ("final_entries", C.c_uint64), ("final_edges", C.c_uint64),
+        ("final_launches", C.c_uint64),
     ]
 
 

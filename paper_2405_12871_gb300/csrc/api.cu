@@ -1412,6 +1412,8 @@ struct Scheduler {
     double ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     double kms[4] = {0, 0, 0, 0};
     uint64_t reach_launches = 0;
+    double final_kms = 0.0;
+    uint64_t final_launches = 0;
 
     explicit Scheduler(imin_ctx *c) : ctx(c) { d_cov.ensure(ctx, 16); }
 
@@ -1563,6 +1565,8 @@ struct Scheduler {
             const FinalStats st = final_estimates(ctx, fsp);
             kms[0] += st.kernel_ms;
             reach_launches += st.launches;
+            final_kms += st.kernel_ms;
+            final_launches += st.launches;
         }
         const double dt_fin = t_fin.ms();
         for (size_t i = 0; i < sp.size(); ++i) {
@@ -1587,6 +1591,8 @@ struct Scheduler {
                 res->edges_scanned += e.edges;
                 res->reach_nodes += e.nodes;
                 res->reach_edges += e.edges;
+                res->final_entries += e.nodes;
+                res->final_edges += e.edges;
                 res->I_after[c] = e.I;
                 res->n_final[c] = e.N;
             }
@@ -1717,7 +1723,7 @@ void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
                 size_t freeb = 0, totalb = 0;
                 cudaMemGetInfo(&freeb, &totalb);
                 cudaGetLastError();
-                freeb += ctx->slots.bytes + ctx->slots_lower.bytes + ctx->big_slots.bytes;
+                freeb += ctx->slots.bytes + ctx->slots_lower.bytes + ctx->big_slots.bytes + ctx->slots_final.bytes;
                 if (freeb < totalb / 4) break;
             }
             sch.add(all[next++]);
@@ -1738,6 +1744,8 @@ void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
         if (!any) I->res->ms_stage[7] = total.ms();
         for (int i = 0; i < 4; ++i) I->res->kernel_ms[i] = sch.kms[i];
         I->res->reach_launches = sch.reach_launches;
+        I->res->final_kernel_ms = sch.final_kms;
+        I->res->final_launches = sch.final_launches;
         I->res->kernel_launches = g_kernel_launches - launches0;
     }
 }

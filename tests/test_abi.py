@@ -54,6 +54,7 @@ int main(void) {
   F(imin_result, nVs); F(imin_result, I_hat); F(imin_result, I_after); F(imin_result, n_spread);
   F(imin_result, n_final); F(imin_result, worlds_sampled); F(imin_result, ms_stage);
   F(imin_result, kernel_ms); F(imin_result, kernel_launches);
+  F(imin_result, final_kernel_ms); F(imin_result, final_launches);
   return 0;
 }
 """
@@ -78,7 +79,7 @@ def test_struct_layouts_match_header(tmp_path):
         else:
             assert getattr(m[t], f).offset == int(v), (t, f)
         n += 1
-    assert n == 22
+    assert n == 24
 
 
 def test_no_gpu_reports_device_error():
