@@ -10,8 +10,11 @@ rank samples its own range with the library; one sum all-reduce then merges:
 * the scalar totals (total spread, edges scanned, non-empty LRR sets);
 * the per-world spreads, gathered in world order.
 
-On a box with one GPU per query this runs as independent replicas (``bench.py --gpus
-N``); the merge logic itself is exercised with CPU ranks over the ``gloo`` backend.
+Max-Coverage over sample stores sharded the same way exchanges one gain vector per
+round (``max_coverage_sharded``).  Collective buffers live on the rank's GPU under
+NCCL and on the host under gloo.  On a box with one GPU per query this runs as
+independent replicas (``bench.py --gpus N``); the merge and exchange logic is
+exercised with CPU ranks over the ``gloo`` backend.
 """
 from __future__ import annotations
 
@@ -86,3 +89,52 @@ def sample_sharded(sample, S, blocked=(), theta=1, first=0, per_world=False, gro
         out["world_spread"] = np.concatenate(
             [g.cpu().numpy()[:s] for g, s in zip(gathered, sizes)]).astype(np.uint32)
     return out
+
+
+def max_coverage_sharded(off, elem, n, k, group=None):
+    """Procedure Max-Coverage (Algorithm 4) over a collection of sets that is sharded
+    across the ranks of ``group``: this rank holds sets ``elem[off[i]:off[i+1]]``
+    (node ids in [0, n)), e.g. the CP or LRR sets of its own world range.
+
+    Each round exchanges one sum all-reduce of the per-node gains (the number of this
+    rank's uncovered sets that contain the node), so that every rank sees the global
+    marginal coverage and picks the same node: the largest gain, ties to the smaller
+    id, no pick at zero gain.  Each rank then covers its own sets that contain the
+    pick and lowers its local gains.  Returns (B, cov, topk) with cov[i] = Cov(B_i)
+    and topk[i] the sum of the k largest global gains in state B_i -- on every rank,
+    equal to one Max-Coverage over the union of the shards."""
+    import torch
+    import torch.distributed as dist
+
+    dev = collective_device(group)
+    off = np.asarray(off, dtype=np.int64)
+    elem = np.asarray(elem, dtype=np.int64)
+    nsets = off.shape[0] - 1
+    gain = np.bincount(elem, minlength=n).astype(np.int64)
+    # inverted index node -> local sets
+    set_of = np.repeat(np.arange(nsets, dtype=np.int64), np.diff(off))
+    order = np.argsort(elem, kind="stable")
+    inv_sets = set_of[order]
+    inv_off = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(elem, minlength=n), out=inv_off[1:])
+    covered = np.zeros(max(nsets, 1), dtype=bool)
+    B, cov, topk = [], [0], []
+    for i in range(k + 1):
+        t = torch.from_numpy(gain.copy()).to(dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        g = t.cpu().numpy()
+        topk.append(int(np.sort(g)[::-1][:k].sum()))
+        if i == k:
+            break
+        u = int(np.argmax(g))              # first index of the maximum: ties to the smaller id
+        if g[u] <= 0:
+            break
+        B.append(u)
+        cov.append(cov[-1] + int(g[u]))
+        for s in inv_sets[inv_off[u]:inv_off[u + 1]]:
+            if covered[s]:
+                continue
+            covered[s] = True
+            np.subtract.at(gain, elem[off[s]:off[s + 1]], 1)
+    return (np.asarray(B, dtype=np.int32), np.asarray(cov, dtype=np.uint64),
+            np.asarray(topk, dtype=np.uint64))

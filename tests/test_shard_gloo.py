@@ -133,3 +133,77 @@ def test_collective_buffers_follow_the_backend(monkeypatch):
     assert shard.collective_device() == torch.device("cuda", 3)
     monkeypatch.setattr(dist, "get_backend", lambda group=None: "gloo")
     assert shard.collective_device() == torch.device("cpu")
+
+
+def _world_sets(seed=5, worlds=120):
+    """CP sets (dominator chains, Algorithm 2) and LRR sets (Algorithm 3) of explicit
+    worlds of a small graph, built from the oracle's one-world routine."""
+    g = synth.erdos_renyi(300, 1500, seed=seed)
+    S = synth.seeds_uniform(g.n, 4, seed=seed + 1)
+    og = oracle.OracleGraph.from_graph(g)
+    Vs = og.vs(S)
+    cp, lrr = [], []
+    for j in range(worlds):
+        live = np.array([og.edge_live(e, 3, j, 1) for e in range(g.m)], np.uint8)
+        t = int(Vs[oracle.target_index(3, j, 1, 0, len(Vs))])
+        w = og.world_explicit(live, S, target=t)
+        seeds = set(int(s) for s in S)
+        for v in np.flatnonzero(w["reached"]):
+            if int(v) in seeds:
+                continue
+            chain, cur = [], int(v)
+            while cur >= 0 and cur not in seeds:
+                chain.append(cur)
+                cur = int(w["idom"][cur])
+            cp.append(chain)
+        lr = [int(x) for x in np.flatnonzero(w["lrr"])]
+        if lr:
+            lrr.append(lr)
+    return g.n, cp, lrr
+
+
+def _csr(sets):
+    off = np.zeros(len(sets) + 1, np.int64)
+    for i, s in enumerate(sets):
+        off[i + 1] = off[i] + len(s)
+    elem = np.concatenate([np.asarray(s, np.int64) for s in sets]) if sets else np.zeros(0, np.int64)
+    return off, elem
+
+
+def _greedy_worker(rank, ws, port, results):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws,
+                            timeout=timedelta(seconds=120))
+    try:
+        rng = np.random.default_rng(8)
+        n = 400
+        rand_sets = [list(rng.choice(n, int(rng.integers(1, 12)), replace=False)) for _ in range(2000)]
+        n2, cp, lrr = _world_sets()
+        for ci, (nn, sets, k) in enumerate(((n, rand_sets, 25), (n2, cp, 10), (n2, lrr, 10),
+                                            (n2, lrr[:3], 10))):
+            # the shards: an uneven split of the sets in order (a rank's world range)
+            cut = (len(sets) * 2) // 5
+            mine = sets[:cut] if rank == 0 else sets[cut:]
+            off, elem = _csr(mine)
+            B, cov, topk = shard.max_coverage_sharded(off, elem, nn, k)
+            wB, wcov, wtopk = oracle.max_coverage_sets(sets, nn, k)
+            assert np.array_equal(B, wB), (ci, B, wB)
+            assert np.array_equal(cov, wcov), ci
+            assert np.array_equal(topk, wtopk), ci
+        if rank == 0:
+            results.put("ok")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_max_coverage_matches_one_rank():
+    """Max-Coverage over sets split across two ranks, with one gain all-reduce per
+    round, picks the same blockers with the same Cov(B_i) and top-k sums as one
+    Max-Coverage over all sets (random set systems, the CP and LRR sets of explicit
+    worlds, and a case that stops early at zero gain)."""
+    import torch.multiprocessing as mp
+    oracle.lib()
+    ctx = mp.get_context("spawn")
+    q = ctx.SimpleQueue()
+    mp.start_processes(_greedy_worker, args=(2, _free_port(), q), nprocs=2, join=True, start_method="spawn")
+    assert q.get() == "ok"
