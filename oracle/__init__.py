@@ -111,6 +111,10 @@ def lib():
                                    C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
                                    C.c_int32, C.c_uint64, _P(C.c_int32), _P(C.c_int32),
                                    _P(C.c_int32), _P(C.c_int32), _P(OResult)]
+        for f in ("oracle_advanced_greedy", "oracle_greedy_replace"):
+            getattr(L, f).argtypes = [C.c_void_p, _P(C.c_int32), C.c_int32, C.c_int32, C.c_uint64,
+                                      C.c_uint64, _P(C.c_int32), _P(C.c_int32)]
+            getattr(L, f).restype = C.c_int32
         L.oracle_result_size.restype = C.c_int32
         assert L.oracle_result_size() == C.sizeof(OResult), "OResult layout mismatch"
         _lib = L
@@ -222,6 +226,17 @@ class OracleGraph:
         N = lib().oracle_stop_rule(self._h, _ptr(S, C.c_int32), len(S), _ptr(B, C.c_int32),
                                    len(B), beta, dprime, key, tag, inst, C.byref(I))
         return int(N), float(I.value)
+
+    def dt_baseline(self, which, S, k, theta, key=0):
+        """AdvancedGreedy (``which='ag'``) or GreedyReplace (``'gr'``) of Xie et al. as
+        the paper describes them: (blockers in order, number of estimates)."""
+        S = _i32(S)
+        B = np.zeros(max(int(k), 1), np.int32)
+        calls = C.c_int32(0)
+        f = lib().oracle_advanced_greedy if which == "ag" else lib().oracle_greedy_replace
+        nb = f(self._h, _ptr(S, C.c_int32), len(S), int(k), int(theta), int(key), _ptr(B, C.c_int32),
+               C.byref(calls))
+        return [int(x) for x in B[:nb]], int(calls.value)
 
     def solve(self, S, k, eps, delta, beta=0.1, gamma=0.1, key=0, inst=0, variant="sandimin",
               fixed_theta=0):

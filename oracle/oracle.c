@@ -1145,5 +1145,122 @@ int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, do
     return 0;
 }
 
+/* ====================================================================== */
+/* The dominator-tree baselines of Xie et al. as the paper describes them   */
+/* (Sec. 2.3): the estimate of D_s(v | B) is the average size of v's        */
+/* subtree in the dominator tree of a live-edge world of G[V \ B] (Example */
+/* 2.1).  AdvancedGreedy adds the best node k times.  GreedyReplace first   */
+/* fills B from the seeds' out-neighbours (up to min(d_out, k) nodes), then */
+/* takes the blockers out in reverse insertion order, each time putting     */
+/* back the best node of V \ S, and returns as soon as the node put back is */
+/* the one taken out.                                                       */
+/* Readings: every estimate draws theta new worlds, estimate number c using */
+/* worlds [c theta, (c+1) theta) of stream tag 8 (which no solve uses);     */
+/* ties go to the smaller node id; no node is added when every estimate is  */
+/* zero.  The second stage walks the blockers of the first stage, newest    */
+/* first.                                                                   */
+/* ====================================================================== */
+#define BASELINE_TAG 8u
+
+/* summed subtree sizes of every node over theta worlds of G[V \ B] */
+static void dt_estimate(const OGraph *g, const int32_t *S, int32_t nS, const int32_t *B, int32_t nB,
+                        uint64_t theta, uint64_t key, uint64_t call, uint64_t *est)
+{
+    Work *w = work_new(g, S, nS, B, nB);
+    SetColl cp;
+    coll_init(&cp);
+    memset(est, 0, sizeof(uint64_t) * (size_t)g->n);
+    for (uint64_t t = 0; t < theta; ++t) {
+        World wd = {NULL, key, call * theta + t, BASELINE_TAG, 0};
+        cp.nsets = 0;
+        cp.off[0] = 0;
+        world_local_sampling(g, w, &wd, S, nS, &cp);
+        /* the CP sets containing v are the worlds' nodes in v's subtree */
+        for (int64_t p = 0; p < cp.off[cp.nsets]; ++p) est[cp.elem[p]] += 1;
+    }
+    coll_free(&cp);
+    work_free(w);
+}
+
+/* the allowed node of largest estimate (smaller id on ties), -1 if all are 0 */
+static int32_t best_node(const OGraph *g, const uint64_t *est, const uint8_t *allowed)
+{
+    int32_t u = -1;
+    uint64_t best = 0;
+    for (int32_t v = 0; v < g->n; ++v)
+        if (allowed[v] && est[v] > best) { best = est[v]; u = v; }
+    return u;
+}
+
+int32_t oracle_advanced_greedy(const OGraph *g, const int32_t *S, int32_t nS, int32_t k, uint64_t theta,
+                               uint64_t key, int32_t *B, int32_t *calls)
+{
+    uint64_t *est = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)g->n + 1));
+    uint8_t *allowed = (uint8_t *)malloc((size_t)g->n + 1);
+    int32_t nb = 0, c = 0;
+    for (int32_t r = 0; r < k; ++r) {
+        dt_estimate(g, S, nS, B, nb, theta, key, (uint64_t)c++, est);
+        memset(allowed, 1, (size_t)g->n);
+        for (int32_t i = 0; i < nS; ++i) allowed[S[i]] = 0;
+        for (int32_t i = 0; i < nb; ++i) allowed[B[i]] = 0;
+        int32_t u = best_node(g, est, allowed);
+        if (u < 0) break;
+        B[nb++] = u;
+    }
+    *calls = c;
+    free(est); free(allowed);
+    return nb;
+}
+
+int32_t oracle_greedy_replace(const OGraph *g, const int32_t *S, int32_t nS, int32_t k, uint64_t theta,
+                              uint64_t key, int32_t *B, int32_t *calls)
+{
+    int32_t n = g->n;
+    uint64_t *est = (uint64_t *)malloc(sizeof(uint64_t) * ((size_t)n + 1));
+    uint8_t *allowed = (uint8_t *)malloc((size_t)n + 1);
+    uint8_t *is_seed = (uint8_t *)calloc((size_t)n + 1, 1);
+    uint8_t *on = (uint8_t *)calloc((size_t)n + 1, 1);
+    int32_t *rest = (int32_t *)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * ((size_t)k + 1));
+    for (int32_t i = 0; i < nS; ++i) is_seed[S[i]] = 1;
+    int32_t d_out = 0;
+    for (int32_t i = 0; i < nS; ++i)
+        for (int64_t e = g->row_ptr[S[i]]; e < g->row_ptr[S[i] + 1]; ++e) {
+            int32_t v = g->col[e];
+            if (g->thr[e] > 0 && !is_seed[v] && !on[v]) { on[v] = 1; d_out++; }
+        }
+    int32_t c = 0, nb = 0;
+    int32_t target = d_out < k ? d_out : k;
+    /* stage 1: candidates = out-neighbours of the seeds */
+    while (nb < target) {
+        dt_estimate(g, S, nS, B, nb, theta, key, (uint64_t)c++, est);
+        for (int32_t v = 0; v < n; ++v) allowed[v] = on[v];
+        for (int32_t i = 0; i < nb; ++i) allowed[B[i]] = 0;
+        int32_t u = best_node(g, est, allowed);
+        if (u < 0) break;
+        B[nb++] = u;
+    }
+    /* stage 2: replacement in reverse insertion order */
+    for (int32_t i = 0; i < nb; ++i) order[i] = B[nb - 1 - i];
+    int32_t nstage1 = nb;
+    for (int32_t r = 0; r < nstage1; ++r) {
+        int32_t out = order[r];
+        int32_t nr = 0;
+        for (int32_t i = 0; i < nb; ++i)
+            if (B[i] != out) rest[nr++] = B[i];
+        dt_estimate(g, S, nS, rest, nr, theta, key, (uint64_t)c++, est);
+        for (int32_t v = 0; v < n; ++v) allowed[v] = !is_seed[v];
+        for (int32_t i = 0; i < nr; ++i) allowed[rest[i]] = 0;
+        int32_t u = best_node(g, est, allowed);
+        if (u < 0 || u == out) break;
+        for (int32_t i = 0; i < nr; ++i) B[i] = rest[i];
+        B[nr] = u;
+        nb = nr + 1;
+    }
+    *calls = c;
+    free(est); free(allowed); free(is_seed); free(on); free(rest); free(order);
+    return nb;
+}
+
 /* size of the result struct, for the binding's layout check */
 int32_t oracle_result_size(void) { return (int32_t)sizeof(OResult); }

@@ -42,3 +42,19 @@ def test_er1k_matches_oracle(ctx, algo):
     assert got == want
     assert len(got[0]) == 5
     G.free()
+
+
+@pytest.mark.parametrize("algo", ["ag", "gr"])
+def test_cl5k_matches_the_oracles_own_ag_gr(ctx, algo):
+    """The package's AG / GR over the library's sampler against the oracle's separate C
+    implementation over its own worlds."""
+    g = synth.chung_lu(5000, 10.0, 2.1, seed=11)
+    S = synth.seeds_top_outdeg(g, 8, 0.01, seed=12)
+    G = ctx.load_graph(g)
+    og = oracle.OracleGraph.from_graph(g)
+    if algo == "ag":
+        got = baselines.advanced_greedy(G.sample, g.n, S, k=6, theta=500, key=3)
+    else:
+        got = baselines.greedy_replace(G.sample, g, S, k=6, theta=500, key=3)
+    assert got[:2] == og.dt_baseline(algo, S, 6, 500, key=3)
+    G.free()
