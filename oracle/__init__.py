@@ -111,6 +111,12 @@ def lib():
                                    C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
                                    C.c_int32, C.c_uint64, _P(C.c_int32), _P(C.c_int32),
                                    _P(C.c_int32), _P(C.c_int32), _P(OResult)]
+        L.oracle_sample_useq.argtypes = [C.c_void_p, _P(C.c_int32), C.c_int32, _P(C.c_int32), C.c_int32,
+                                         _P(C.c_int32), C.c_int32, C.c_uint64, C.c_uint64, C.c_uint32,
+                                         C.c_uint32, C.c_uint64, _P(C.c_uint64), _P(C.c_uint64),
+                                         _P(C.c_uint64)]
+        L.oracle_useq_explicit.argtypes = [C.c_void_p, _P(C.c_uint8), _P(C.c_int32), C.c_int32,
+                                           _P(C.c_int32), C.c_int32, _P(C.c_uint64), _P(C.c_uint64)]
         for f in ("oracle_advanced_greedy", "oracle_greedy_replace"):
             getattr(L, f).argtypes = [C.c_void_p, _P(C.c_int32), C.c_int32, C.c_int32, C.c_uint64,
                                       C.c_uint64, _P(C.c_int32), _P(C.c_int32)]
@@ -226,6 +232,30 @@ class OracleGraph:
         N = lib().oracle_stop_rule(self._h, _ptr(S, C.c_int32), len(S), _ptr(B, C.c_int32),
                                    len(B), beta, dprime, key, tag, inst, C.byref(I))
         return int(N), float(I.value)
+
+    def lrr_sequences(self, S, blocked=(), query=(), theta=1, key=0, tag=0, inst=0, first=0):
+        """LRR sequences of worlds [first, first + theta): per-node sequence credit
+        (|M_phi({u})| summed over worlds), per-world |M_phi(query)|, and the totals
+        (elements = sum of |L(v)|, cov = sum of the per-world values, nodes reached)."""
+        S, B, Q = _i32(S), _i32(blocked), _i32(query)
+        credit = np.zeros(self.n, np.uint64)
+        cw = np.zeros(max(int(theta), 1), np.uint64)
+        scal = np.zeros(3, np.uint64)
+        lib().oracle_sample_useq(self._h, _ptr(S, C.c_int32), len(S), _ptr(B, C.c_int32), len(B),
+                                 _ptr(Q, C.c_int32), len(Q), int(theta), int(key), int(tag), int(inst),
+                                 int(first), _ptr(credit, C.c_uint64), _ptr(cw, C.c_uint64),
+                                 _ptr(scal, C.c_uint64))
+        return dict(credit_useq=credit, cov_world=cw[: int(theta)], elements=int(scal[0]), cov=int(scal[1]),
+                    total_spread=int(scal[2]))
+
+    def lrr_sequence_explicit(self, live_mask, S, query=()):
+        live_mask = np.ascontiguousarray(np.asarray(live_mask, dtype=np.uint8))
+        S, Q = _i32(S), _i32(query)
+        credit = np.zeros(self.n, np.uint64)
+        scal = np.zeros(3, np.uint64)
+        lib().oracle_useq_explicit(self._h, _ptr(live_mask, C.c_uint8), _ptr(S, C.c_int32), len(S),
+                                   _ptr(Q, C.c_int32), len(Q), _ptr(credit, C.c_uint64), _ptr(scal, C.c_uint64))
+        return dict(credit_useq=credit, elements=int(scal[0]), cov=int(scal[1]), total_spread=int(scal[2]))
 
     def dt_baseline(self, which, S, k, theta, key=0):
         """AdvancedGreedy (``which='ag'``) or GreedyReplace (``'gr'``) of Xie et al. as

@@ -696,6 +696,81 @@ int oracle_sample(const OGraph *g, const int32_t *S, int32_t nS, const int32_t *
     return 0;
 }
 
+/* ====================================================================== */
+/* LRR sequences (Sec. 4.2, "Discussion" after Algorithm 3): in world phi,  */
+/* the LRR set L_phi(v) of EVERY node v of R_phi(s) \ S, each by its own   */
+/* reverse traversal of phi^s (the one-per-reached-node cost the paper's    */
+/* Table 2 measures).  Per world:                                            */
+/*   credit_useq[u] += |{v : u in L_phi(v)}| (= |M_phi({u})|),              */
+/*   elements += sum over v of |L_phi(v)|,                                   */
+/*   cov = |{v : L_phi(v) meets Q}| (= |M_phi(Q)|, the world's term of       */
+/*   Cov_{L^s}(Q), whose mean over worlds is D^U(Q)).                        */
+/* ====================================================================== */
+static uint64_t world_lrr_sequence(const OGraph *g, Work *w, const World *wd, const int32_t *S,
+                                   int32_t nS, const uint8_t *inQ, uint64_t *credit_useq,
+                                   uint64_t *elements, int32_t *R_out)
+{
+    int32_t R = world_reach(g, w, wd, S, nS);
+    uint64_t cov = 0;
+    for (int32_t i = 0; i < R; ++i) {
+        int32_t v = w->queue[i];
+        if (w->is_seed[v]) continue;
+        int32_t L = lrr_from_target(g, w, wd, v);
+        int meets = 0;
+        for (int32_t q = 0; q < L; ++q) {
+            int32_t u = w->queue2[q];
+            if (credit_useq) credit_useq[u] += 1;
+            if (inQ && inQ[u]) meets = 1;
+        }
+        *elements += (uint64_t)L;
+        cov += (uint64_t)meets;
+    }
+    if (R_out) *R_out = R;
+    return cov;
+}
+
+/* worlds [first, first + theta) of (key, tag, inst), blocked set B, query set Q;
+ * counts are ADDED into credit_useq; cov_world[t] = |M_phi(Q)| of world first + t;
+ * scal[0] = sum of |L(v)|, scal[1] = sum of cov_world, scal[2] = sum |R_j|. */
+int oracle_sample_useq(const OGraph *g, const int32_t *S, int32_t nS, const int32_t *B, int32_t nB,
+                       const int32_t *Q, int32_t nQ, uint64_t theta, uint64_t key, uint32_t tag,
+                       uint32_t inst, uint64_t first, uint64_t *credit_useq, uint64_t *cov_world,
+                       uint64_t *scal)
+{
+    Work *w = work_new(g, S, nS, B, nB);
+    uint8_t *inQ = (uint8_t *)calloc((size_t)g->n + 1, 1);
+    for (int32_t i = 0; i < nQ; ++i) inQ[Q[i]] = 1;
+    scal[0] = scal[1] = scal[2] = 0;
+    for (uint64_t t = 0; t < theta; ++t) {
+        World wd = {NULL, key, first + t, tag, inst};
+        int32_t R = 0;
+        uint64_t c = world_lrr_sequence(g, w, &wd, S, nS, inQ, credit_useq, &scal[0], &R);
+        if (cov_world) cov_world[t] = c;
+        scal[1] += c;
+        scal[2] += (uint64_t)R;
+    }
+    free(inQ);
+    work_free(w);
+    return 0;
+}
+
+/* the same for one explicit world (live_mask[e] = 1 if edge e is live) */
+int oracle_useq_explicit(const OGraph *g, const uint8_t *live_mask, const int32_t *S, int32_t nS,
+                         const int32_t *Q, int32_t nQ, uint64_t *credit_useq, uint64_t *scal)
+{
+    Work *w = work_new(g, S, nS, NULL, 0);
+    uint8_t *inQ = (uint8_t *)calloc((size_t)g->n + 1, 1);
+    for (int32_t i = 0; i < nQ; ++i) inQ[Q[i]] = 1;
+    World wd = {live_mask, 0, 0, 0, 0};
+    int32_t R = 0;
+    scal[0] = 0;
+    scal[1] = world_lrr_sequence(g, w, &wd, S, nS, inQ, credit_useq, &scal[0], &R);
+    scal[2] = (uint64_t)R;
+    free(inQ);
+    work_free(w);
+    return 0;
+}
+
 /* V'_s as an API (count returned; nodes written to out[] ascending). */
 int32_t oracle_vs(const OGraph *g, const int32_t *S, int32_t nS, const int32_t *B, int32_t nB,
                   int32_t *out)
