@@ -477,6 +477,90 @@ def run_rmat(args):
 
 
 # ---------------------------------------------------------------------------
+def run_final_only(args):
+    """Profiling case for the fused final-estimate kernel: the final estimates
+    (Algorithm 1, line 4) of three blocker sets on the CL-1M workload through
+    imin_final_estimates alone, so that the process holds only the graph and the fused
+    kernel's slots.  The sets: the top 100 of the seeds' out-neighbours by
+    q(v) * outdeg(v) (LHGA's rule), by q(v), and the 100 largest out-degrees."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    g, S, cfg = synth.workload_cl1m()
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    G = ctx.load_graph(g)
+    Sset = set(int(s) for s in S)
+    pq = np.ceil(g.prob.astype(np.float64) * 16777216.0) / 16777216.0
+    prod = {}
+    for s in S:
+        for e in range(int(g.row_ptr[s]), int(g.row_ptr[s + 1])):
+            v = int(g.col[e])
+            if pq[e] > 0 and v not in Sset:
+                prod[v] = prod.get(v, 1.0) * (1.0 - pq[e])
+    outdeg = np.diff(g.row_ptr)
+    on = sorted(prod)
+    by_score = sorted(on, key=lambda v: (-(1.0 - prod[v]) * outdeg[v], v))[:cfg["k"]]
+    by_q = sorted(on, key=lambda v: (-(1.0 - prod[v]), v))[:cfg["k"]]
+    order = np.lexsort((np.arange(g.n), -outdeg))
+    by_deg = [int(v) for v in order if int(v) not in Sset][:cfg["k"]]
+    cands = [sorted(by_score), sorted(by_q), sorted(by_deg)]
+    for it in range(2):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        I, N = G.final_estimates(S, cands, gamma=0.1, delta=cfg["delta"], key=cfg["key"], spread_hint=18314.0)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "final-only", "s": time.perf_counter() - a, "I_after": I, "n_worlds": N}),
+              flush=True)
+    G.free()
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_useq(args):
+    """The LRR-sequence estimator of D^U (Sec. 4.2, Discussion; every reached node's
+    LRR set per world) against Global Sampling (Algorithm 3; one LRR set per world) on
+    the CL-1M query, for the blocker set B_U of a solve: time per world and per-world
+    variance of each estimate of D^U(B_U), and the time each needs for the same
+    standard error.  GS's per-world estimate is |V'_s| times a Bernoulli(D^U/|V'_s|)
+    indicator, so its variance is D^U (|V'_s| - D^U); D^U is taken from the sequence
+    estimate, which is far tighter."""
+    import torch
+    from paper_2405_12871_gb300 import _lib, synth
+    g, S, cfg = synth.workload_cl1m()
+    ctx = _lib.Context(0, stream=torch.cuda.current_stream().cuda_stream)
+    G = ctx.load_graph(g)
+    kw = dict(k=cfg["k"], eps=cfg["eps"], delta=cfg["delta"], key=cfg["key"])
+    G.solve(S, **kw)
+    r = G.solve(S, **kw)
+    BU = [int(x) for x in r["B_U"]]
+    theta = args.useq_worlds
+    G.lrr_sequences(S, query=BU, theta=64, key=1, tag=11, first=10_000_000)
+    torch.cuda.synchronize()
+    a = time.perf_counter()
+    q = G.lrr_sequences(S, query=BU, theta=theta, key=1, tag=11)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - a
+    cw = q["cov_world"].astype(np.float64)
+    du = float(cw.mean())
+    var_seq = float(cw.var(ddof=1))
+    nvs = int(r["nVs"])
+    var_gs = du * (nvs - du)
+    gs_worlds = int(r["theta_L1"] + r["theta_L2"])
+    t_gs = r["kernel_ms"][2] / 1e3 / max(gs_worlds, 1)
+    out = {"mode": "lrr-sequences", "workload": "chung-lu-1M", "query": "B_U of the solve (k = 100)",
+           "worlds": theta, "seq_s_per_world": t_seq / theta, "seq_elements_per_world": q["elements"] / theta,
+           "seq_nodes_per_world": q["total_spread"] / theta, "DU_seq": du, "DU_seq_rel_stderr":
+           float(np.sqrt(var_seq / theta) / du), "DU_gs_solve": r["DU_hat"], "nVs": nvs,
+           "var_per_world_seq": var_seq, "var_per_world_gs": var_gs,
+           "gs_s_per_world": t_gs, "gs_worlds_in_solve": gs_worlds,
+           "time_for_equal_stderr_gs_over_seq": (var_gs * t_gs) / (var_seq * (t_seq / theta))}
+    print(json.dumps(out), flush=True)
+    G.free()
+    ctx.close()
+    return 0
+
+
+# ---------------------------------------------------------------------------
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -502,6 +586,11 @@ def main():
                     help="worlds per AG / GR estimate")
     ap.add_argument("--baseline-eval", type=int, default=100_000,
                     help="worlds of the final spread re-estimate")
+    ap.add_argument("--useq", action="store_true",
+                    help="the LRR-sequence estimator against Global Sampling on the CL-1M query")
+    ap.add_argument("--useq-worlds", type=int, default=2000)
+    ap.add_argument("--final-only", action="store_true",
+                    help="profiling case: the fused final estimates of three blocker sets on CL-1M alone")
     ap.add_argument("--rmat", action="store_true",
                     help="the R-MAT-4M configuration: reach-only sampling roofline and timed solves")
     ap.add_argument("--rmat-worlds", type=int, default=2000)
@@ -525,6 +614,10 @@ def main():
         return run_sweep(args)
     if args.rmat:
         return run_rmat(args)
+    if args.final_only:
+        return run_final_only(args)
+    if args.useq:
+        return run_useq(args)
 
     import torch
     import torch.distributed as dist

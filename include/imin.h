@@ -153,6 +153,41 @@ typedef struct imin_sample_out {
 int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *blocked, int32_t nB,
                 uint64_t theta, const imin_sample_opts *opts, imin_sample_out *out);
 
+/* Final estimates (Algorithm 1, line 4) of given blocker sets: for each of n_cand
+ * (1..3) candidate sets B[c] (host int32[nB[c]], distinct, disjoint from S), the
+ * (gamma, delta)-estimate of E[I_{G[V \ B[c]}](s)] by the stopping rule (the reading
+ * imin_solve uses), all on the worlds of stream tag 5 of (key, inst): the same values
+ * imin_solve reports in I_after / n_final for its candidates.  One traversal per world
+ * serves every candidate.  spread_hint: the expected spread without blockers if known
+ * (sizes the traversal queue; 0 = unknown).  Outputs: I_after[n_cand], n_worlds[n_cand]
+ * (the N each stopping rule chose).  Errors: IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM,
+ * IMIN_EDEVICE. */
+int imin_final_estimates(imin_graph *g, const int32_t *S, int32_t nS, int32_t n_cand, const int32_t *const *B,
+                         const int32_t *nB, double gamma, double delta, uint64_t key, uint32_t inst,
+                         double spread_hint, double *I_after, uint64_t *n_worlds);
+
+/* LRR sequences (Sec. 4.2, "Discussion" after Algorithm 3): for each world j of
+ * [first_sample, first_sample + theta) of the stream (opts->key, tag, inst), the LRR
+ * set L_phi(v) of EVERY node v of phi^s = R_phi(s) \ S (the nodes of phi^s that
+ * reach v inside phi^s), one reverse traversal per node -- the estimator of D^U the
+ * paper finds too slow on a CPU (Table 2) and replaces by Global Sampling.
+ *   S, nS          seeds (as imin_sample); blocked, nB: nodes never entered
+ *   query, nQ      host int32[nQ] (NULL if nQ = 0), distinct node ids: the set Q whose
+ *                  coverage Cov_{L^s}(Q) is counted
+ *   opts           key, tag, inst, first_sample as imin_sample (mode is ignored)
+ *   credit_useq    HOST uint64[n] or NULL: sum over worlds of |{v : u in L_phi(v)}|
+ *                  (= |M_phi({u})|, the nodes of phi^s that u reaches)
+ *   cov_world      HOST uint64[theta] or NULL: per world, |{v : L_phi(v) meets Q}|
+ *                  (= |M_phi(Q)|; its mean over worlds estimates D^U(Q) without bias)
+ *   totals         HOST uint64[5]: sum of |L_phi(v)|, sum of cov_world, nodes reached
+ *                  (seeds included), edges scanned, worlds
+ * Outputs are written only on success.  Errors: IMIN_EINVAL, IMIN_ERANGE (world
+ * index >= 2^32, or a world with more live edges inside its reach set than a
+ * slot holds), IMIN_ENOMEM, IMIN_EDEVICE. */
+int imin_sample_lrr_sequences(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *blocked, int32_t nB,
+                              const int32_t *query, int32_t nQ, uint64_t theta, const imin_sample_opts *opts,
+                              uint64_t *credit_useq, uint64_t *cov_world, uint64_t totals[5]);
+
 /* Options of imin_solve.  Defaults used by the paper (Sec. 6): beta = gamma = 0.1. */
 typedef struct imin_solve_opts {
     double beta;            /* relative error of the spread estimate used by LSBM, in (0,1) */

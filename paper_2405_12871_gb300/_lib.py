@@ -20,6 +20,7 @@ VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 # names the library must export (checked by the CPU tests against include/imin.h)
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
            "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc",
+           "imin_sample_lrr_sequences", "imin_final_estimates",
            "imin_solve_batch", "imin_server_start", "imin_server_submit", "imin_server_poll",
            "imin_server_stop", "imin_graph_tuning"]
 NOALLOC_MAX_NODES = 2_000_000
@@ -119,6 +120,14 @@ def load(build_if_missing: bool = True):
                                             C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint64,
                                             C.c_void_p, C.c_void_p, P(C.c_uint64), C.c_void_p]
     L.imin_sample_reach_noalloc.restype = C.c_int
+    L.imin_sample_lrr_sequences.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), C.c_int32,
+                                            P(C.c_int32), C.c_int32, C.c_uint64, P(SampleOpts),
+                                            P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]
+    L.imin_sample_lrr_sequences.restype = C.c_int
+    L.imin_final_estimates.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, C.c_int32, P(P(C.c_int32)),
+                                       P(C.c_int32), C.c_double, C.c_double, C.c_uint64, C.c_uint32,
+                                       C.c_double, P(C.c_double), P(C.c_uint64)]
+    L.imin_final_estimates.restype = C.c_int
     L.imin_solve_batch.argtypes = [C.c_void_p, C.c_int32, P(Query), P(Result)]
     L.imin_solve_batch.restype = C.c_int
     L.imin_server_start.argtypes = [C.c_void_p, P(ServerOpts), P(C.c_void_p)]
@@ -332,6 +341,41 @@ class Graph:
 
     def solve(self, S, k, eps, delta, **kw):
         return imin_solve(self.ctx.h, self.h, S, k, eps, delta, **kw)
+
+    def final_estimates(self, S, cands, gamma=0.1, delta=0.01, key=0, inst=0, spread_hint=0.0):
+        """imin_final_estimates: (I_after, n_worlds) lists for 1..3 candidate blocker sets."""
+        L = load()
+        S = _as_i32(S)
+        arrs = [_as_i32(b) for b in cands]
+        ptrs = (C.POINTER(C.c_int32) * len(arrs))(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs])
+        lens = (C.c_int32 * len(arrs))(*[len(a) for a in arrs])
+        I = (C.c_double * len(arrs))()
+        N = (C.c_uint64 * len(arrs))()
+        rc = L.imin_final_estimates(self.h, _i32p(S), len(S), len(arrs), ptrs, lens, float(gamma), float(delta),
+                                    int(key), int(inst), float(spread_hint), I, N)
+        _check(self.ctx.h, rc, "imin_final_estimates")
+        return list(I), [int(x) for x in N]
+
+    def lrr_sequences(self, S, blocked=(), query=(), theta=1, key=0, tag=0, inst=0, first=0, credit=True,
+                      per_world=True):
+        """imin_sample_lrr_sequences: the LRR set of every reached node of every world."""
+        L = load()
+        S, B, Q = _as_i32(S), _as_i32(blocked), _as_i32(query)
+        opts = SampleOpts(int(key), int(tag), int(inst), int(first), 0, 0)
+        credit_a = np.zeros(self.n, np.uint64) if credit else None
+        cw = np.zeros(max(int(theta), 1), np.uint64) if per_world else None
+        tot = (C.c_uint64 * 5)()
+        u64p = lambda a: a.ctypes.data_as(C.POINTER(C.c_uint64)) if a is not None else None
+        rc = L.imin_sample_lrr_sequences(self.h, _i32p(S), len(S), _i32p(B), len(B), _i32p(Q), len(Q),
+                                         int(theta), C.byref(opts), u64p(credit_a), u64p(cw), tot)
+        _check(self.ctx.h, rc, "imin_sample_lrr_sequences")
+        out = dict(elements=int(tot[0]), cov=int(tot[1]), total_spread=int(tot[2]), edges_scanned=int(tot[3]),
+                   worlds=int(tot[4]))
+        if credit:
+            out["credit_useq"] = credit_a
+        if per_world:
+            out["cov_world"] = cw[: int(theta)]
+        return out
 
     def tuning(self):
         """The autotuner's reach-only launch choice: dict(ctas, threads, minb, smem_bitmap)."""

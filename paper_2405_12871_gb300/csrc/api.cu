@@ -170,6 +170,7 @@ struct TaskRun {
     QueryDev q;
     uint64_t first = 0;
     uint32_t count = 0;
+    const uint32_t *list = nullptr;   // device: the worlds are first + list[0 .. count) (else consecutive)
     WorldOut out;
     std::function<void(uint32_t)> grow;   // enlarge the task's store for nd worlds; updates out
     unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -421,7 +422,7 @@ struct Runner {
         size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
         std::vector<WTask> ht;
         for (int i = 0; i < n; ++i)
-            ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, nullptr, T[i]->out));
+            ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, T[i]->list, T[i]->out));
         launch(ht, T[0]->g, flags, cfg, arena, layout);
         std::vector<unsigned char> hc((size_t)n * CTL);
         std::vector<uint32_t> claims(n);
@@ -776,6 +777,7 @@ struct FinalSpec {
     double gamma, delta;
     uint64_t key;
     uint32_t inst;
+    double spread_hint;   // expected spread without blockers (sizes the fused queue; 0 = unknown)
     SpreadEst est[3];
 };
 
@@ -860,8 +862,23 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         }
     }
     const int occ = std::max(1, std::min(minb, final_blocks_per_sm(bd)));
+    // queue entries per slot: a world needs at most the three reach sets' sizes; the
+    // queue holds 8 times the expected spread (all 3 (n + 1) when it is not known), and
+    // a world that overflows it is re-run one candidate at a time below
+    double hint = 0.0;
+    int32_t nSmax = 1;
+    for (const FinalSpec &f : specs) {
+        hint = std::max(hint, f.spread_hint > 0.0 ? f.spread_hint : 1e30);
+        nSmax = std::max<int32_t>(nSmax, (int32_t)f.q->S.size());
+    }
+    const double full = 3.0 * ((double)nmax + 1.0);
+    int32_t qcap = (int32_t)std::min(full, std::max(65536.0, 8.0 * hint + 3.0 * nSmax));
+    if (const char *qe = std::getenv("IMIN_FINAL_QCAP")) {   // test hook: tiny queues, many re-runs
+        const long v = std::strtol(qe, nullptr, 10);
+        if (v > nSmax && v < qcap) qcap = (int32_t)v;
+    }
     size_t off_q = 0;
-    const size_t per = final_slot_bytes(nmax, &off_q);
+    const size_t per = final_slot_bytes(nmax, qcap, &off_q);
     size_t freeb = 0, totalb = 0;
     cudaMemGetInfo(&freeb, &totalb);
     size_t avail = freeb / 2;
@@ -870,8 +887,8 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
     size_t ctas = (size_t)ctx->num_sms * occ;
     if (per * ctas > avail) ctas = std::max<size_t>(avail / per, 1);
     if (per > freeb) fail(IMIN_ENOMEM, "not enough device memory for the final estimates");
-    DBuf ctl, cd, dtasks;
-    std::vector<DBuf> sizes(ns);
+    DBuf ctl, cd, dtasks, rerun_ws;
+    std::vector<DBuf> sizes(ns), defl(ns);
     std::vector<std::vector<uint32_t>> hsz(ns);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     IM_CUDA(cudaEventCreate(&e0));
@@ -912,6 +929,9 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
             t.first = first[i];
             t.count = (uint32_t)cnt;
             t.sizes = sizes[i].as<uint32_t>();
+            defl[i].ensure(ctx, (size_t)cnt * 4 + 16);
+            t.deferred = defl[i].as<uint32_t>();
+            t.deferred_cap = (uint32_t)cnt;
             ht.push_back(t);
             idx.push_back(i);
         }
@@ -920,7 +940,10 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         ctl.ensure(ctx, (size_t)nt * 64);
         cd.ensure(ctx, (size_t)nt * 8 + 16);
         dtasks.ensure(ctx, (size_t)nt * sizeof(FTask));
-        for (int k = 0; k < nt; ++k) ht[k].acc = ctl.as<unsigned long long>() + (size_t)k * 8;
+        for (int k = 0; k < nt; ++k) {
+            ht[k].acc = ctl.as<unsigned long long>() + (size_t)k * 8;
+            ht[k].n_deferred = reinterpret_cast<uint32_t *>(ht[k].acc + 6);
+        }
         // the arena is prepared last (an allocation that does not fit drops the cached
         // arenas); nibble maps must start clear, and every world leaves them clear
         {
@@ -939,7 +962,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         IM_CUDA(cudaMemcpyAsync(dtasks.p, ht.data(), ht.size() * sizeof(FTask), cudaMemcpyHostToDevice,
                                 ctx->stream));
         IM_CUDA(cudaEventRecord(e0, ctx->stream));
-        launch_final_tasks(ctx, dtasks.as<FTask>(), nt, nmax, bd, (int)ctas, ctx->slots_final.p,
+        launch_final_tasks(ctx, dtasks.as<FTask>(), nt, nmax, qcap, bd, (int)ctas, ctx->slots_final.p,
                            cd.as<uint32_t>(), cd.as<uint32_t>() + nt);
         IM_CUDA(cudaEventRecord(e1, ctx->stream));
         IM_CUDA(cudaEventSynchronize(e1));
@@ -951,6 +974,66 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         std::vector<uint32_t> claims(nt);
         IM_CUDA(cudaMemcpy(acc.data(), ctl.p, acc.size() * 8, cudaMemcpyDeviceToHost));
         IM_CUDA(cudaMemcpy(claims.data(), cd.p, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+        // worlds that overflowed the fused queue: each candidate's size by its own
+        // reach-only traversal of the same world (tag 5), all in one launch
+        {
+            std::vector<uint32_t> nd(nt);
+            for (int k = 0; k < nt; ++k) std::memcpy(&nd[k], &acc[(size_t)k * 8 + 6], 4);
+            std::vector<TaskRun> rr;
+            std::vector<std::pair<int, int>> rref;
+            size_t wsz = 0;
+            for (int k = 0; k < nt; ++k)
+                if (nd[k])
+                    for (int c = 0; c < 3; ++c)
+                        if ((ht[k].cands >> c) & 1u) wsz += ht[k].count;
+            if (wsz) {
+                rerun_ws.ensure(ctx, wsz * 4 + 16);
+                size_t at = 0;
+                rr.reserve((size_t)nt * 3);
+                for (int k = 0; k < nt; ++k) {
+                    if (!nd[k]) continue;
+                    const size_t i = idx[k];
+                    for (int c = 0; c < 3; ++c) {
+                        if (!((ht[k].cands >> c) & 1u)) continue;
+                        TaskRun t;
+                        t.g = specs[i].g;
+                        t.q = qdev(*specs[i].qb[c], specs[i].key, TAG_FINAL, specs[i].inst);
+                        t.first = ht[k].first;
+                        t.count = nd[k];
+                        t.list = defl[i].as<uint32_t>();
+                        t.out.world_spread = rerun_ws.as<uint32_t>() + at;
+                        at += ht[k].count;
+                        rr.push_back(t);
+                        rref.emplace_back(k, c);
+                    }
+                }
+                std::vector<TaskRun *> rp;
+                for (TaskRun &t : rr) rp.push_back(&t);
+                Runner run(ctx);
+                run.run(rp, WF_SPREAD);
+                fs.kernel_ms += run.kernel_ms;
+                fs.launches += (uint64_t)run.launches;
+                std::vector<uint32_t> hws(wsz), hdef;
+                IM_CUDA(cudaMemcpy(hws.data(), rerun_ws.p, wsz * 4, cudaMemcpyDeviceToHost));
+                at = 0;
+                for (size_t r = 0; r < rr.size(); ++r) {
+                    const int k = rref[r].first, c = rref[r].second;
+                    const size_t i = idx[k];
+                    hdef.resize(nd[k]);
+                    IM_CUDA(cudaMemcpy(hdef.data(), defl[i].p, (size_t)nd[k] * 4, cudaMemcpyDeviceToHost));
+                    // the re-run's sizes sit at the worlds' relative indices
+                    std::vector<uint32_t> szk((size_t)ht[k].count * 4);
+                    IM_CUDA(cudaMemcpy(szk.data(), sizes[i].p, szk.size() * 4, cudaMemcpyDeviceToHost));
+                    for (uint32_t rel : hdef) szk[(size_t)rel * 4 + c] = hws[at + rel];
+                    IM_CUDA(cudaMemcpy(sizes[i].p, szk.data(), szk.size() * 4, cudaMemcpyHostToDevice));
+                    SpreadEst &r0 = specs[i].est[c];
+                    r0.nodes += rr[r].acc[0];
+                    r0.edges += rr[r].acc[1];
+                    r0.worlds += rr[r].acc[4];
+                    at += ht[k].count;
+                }
+            }
+        }
         for (int k = 0; k < nt; ++k) {
             const size_t i = idx[k];
             FinalSpec &f = specs[i];
@@ -1548,6 +1631,7 @@ struct Scheduler {
                 f.delta = I->delta;
                 f.key = I->key;
                 f.inst = I->inst;
+                f.spread_hint = I->I_hat;
                 fsp.push_back(f);
                 fin.push_back(I);
             }
@@ -1976,6 +2060,133 @@ int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *bloc
             if (pws) IM_CUDA(cudaMemcpyAsync(out->world_spread, pws, (size_t)theta * 4, cudaMemcpyDeviceToHost, st));
         }
         IM_CUDA(cudaStreamSynchronize(st));
+    });
+}
+
+int imin_final_estimates(imin_graph *g, const int32_t *S, int32_t nS, int32_t n_cand, const int32_t *const *B,
+                         const int32_t *nB, double gamma, double delta, uint64_t key, uint32_t inst,
+                         double spread_hint, double *I_after, uint64_t *n_worlds)
+{
+    if (!g || !B || !nB || !I_after || !n_worlds || n_cand < 1 || n_cand > 3) return IMIN_EINVAL;
+    imin_ctx *ctx = g->ctx;
+    return run_guarded(ctx, [&] {
+        IM_CUDA(cudaSetDevice(ctx->device));
+        if (!(gamma > 0.0 && gamma < 1.0) || !(delta > 0.0 && delta < 1.0))
+            fail(IMIN_EINVAL, "gamma and delta must lie in (0, 1)");
+        Query q, qb[3];
+        prepare_query(ctx, g, q, S, nS, nullptr, 0, false);
+        FinalSpec f{};
+        f.g = g;
+        f.q = &q;
+        for (int c = 0; c < 3; ++c) {
+            f.qb[c] = &qb[c];
+            f.use[c] = c < n_cand;
+            if (f.use[c]) prepare_query(ctx, g, qb[c], q.S.data(), (int32_t)q.S.size(), B[c], nB[c], true);
+        }
+        f.gamma = gamma;
+        f.delta = delta;
+        f.key = key;
+        f.inst = inst;
+        f.spread_hint = spread_hint > 0.0 ? spread_hint : 0.0;
+        std::vector<FinalSpec> v{f};
+        final_estimates(ctx, v);
+        for (int c = 0; c < n_cand; ++c) {
+            I_after[c] = v[0].est[c].I;
+            n_worlds[c] = v[0].est[c].N;
+        }
+    });
+}
+
+int imin_sample_lrr_sequences(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *blocked, int32_t nB,
+                              const int32_t *query, int32_t nQ, uint64_t theta, const imin_sample_opts *opts,
+                              uint64_t *credit_useq, uint64_t *cov_world, uint64_t totals[5])
+{
+    if (!g || !opts || !totals || (nQ > 0 && !query)) return IMIN_EINVAL;
+    imin_ctx *ctx = g->ctx;
+    return run_guarded(ctx, [&] {
+        IM_CUDA(cudaSetDevice(ctx->device));
+        if (opts->reserved != 0) fail(IMIN_EINVAL, "reserved field must be 0");
+        if (opts->first_sample + theta > ((uint64_t)1 << 32) || theta >= ((uint64_t)1 << 31))
+            fail(IMIN_ERANGE, "world index >= 2^32 or theta >= 2^31");
+        Query q, qq;
+        prepare_query(ctx, g, q, S, nS, blocked, nB, false);
+        std::vector<int32_t> Qv;
+        check_nodes(g, query, nQ, "query set", Qv);
+        const int32_t n = g->n;
+        cudaStream_t st = ctx->stream;
+        DBuf dq, dqbm, dcredit, dcov, dctl, arena;
+        const uint32_t *qbm = nullptr;
+        if (!Qv.empty()) {
+            dq.ensure(ctx, Qv.size() * 4);
+            IM_CUDA(cudaMemcpyAsync(dq.p, Qv.data(), Qv.size() * 4, cudaMemcpyHostToDevice, st));
+            dqbm.ensure(ctx, q.words * 4);
+            fill_bitmap(ctx, dqbm.as<uint32_t>(), q.words, dq.as<int32_t>(), (int32_t)Qv.size());
+            qbm = dqbm.as<uint32_t>();
+        }
+        unsigned long long *pcredit = nullptr, *pcov = nullptr;
+        if (credit_useq) {
+            dcredit.ensure(ctx, (size_t)n * 8);
+            IM_CUDA(cudaMemsetAsync(dcredit.p, 0, (size_t)n * 8, st));
+            pcredit = dcredit.as<unsigned long long>();
+        }
+        if (cov_world && theta > 0) {
+            dcov.ensure(ctx, (size_t)theta * 8);
+            pcov = dcov.as<unsigned long long>();
+        }
+        dctl.ensure(ctx, 128);
+        IM_CUDA(cudaMemsetAsync(dctl.p, 0, 128, st));
+        unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (theta > 0) {
+            // every live pair of a world is an edge of the graph, so m pairs always fit;
+            // the slot holds min(m, max(2^20, 4 (n + 1))) and a world with more fails the call
+            const int32_t ecap = (int32_t)std::min<int64_t>(std::max<int64_t>(g->m, 1),
+                                                            std::max<int64_t>(1 << 20, 4 * ((int64_t)n + 1)));
+            const size_t per = useq_slot_bytes(n, ecap, nullptr);
+            size_t freeb = 0, totalb = 0;
+            cudaMemGetInfo(&freeb, &totalb);
+            size_t avail = freeb / 2;
+            if (ctx->budget)
+                avail = std::min(avail, ctx->budget > ctx->in_use ? (ctx->budget - ctx->in_use) / 2 : 0);
+            size_t ctas = (size_t)ctx->num_sms * (size_t)std::max(1, std::min(2, useq_blocks_per_sm()));
+            ctas = std::min<size_t>(ctas, theta);
+            if (per * ctas > avail) ctas = std::max<size_t>(avail / per, 1);
+            if (per > freeb) fail(IMIN_ENOMEM, "not enough device memory for an LRR-sequence slot");
+            arena.ensure(ctx, per * ctas, false, true);
+            IM_CUDA(cudaMemsetAsync(arena.p, 0, arena.bytes, st));
+            UseqLaunch L{};
+            L.row_ptr = g->row_ptr.as<int32_t>();
+            L.ce = g->ce.as<uint4>();
+            L.n = n;
+            L.S = q.dS.as<int32_t>();
+            L.nS = (int32_t)q.S.size();
+            L.seed_bm = q.dseed_bm.as<uint32_t>();
+            L.blocked_bm = q.blocked.empty() ? nullptr : q.dblk_bm.as<uint32_t>();
+            L.query_bm = qbm;
+            L.key = opts->key;
+            L.tag = opts->tag;
+            L.inst = opts->inst;
+            L.first = opts->first_sample;
+            L.count = (uint32_t)theta;
+            L.claim = reinterpret_cast<uint32_t *>(dctl.as<char>() + 64);
+            L.slot_base = arena.p;
+            L.ecap = ecap;
+            L.ctas = (int)ctas;
+            L.credit = pcredit;
+            L.cov_world = pcov;
+            L.acc = dctl.as<unsigned long long>();
+            L.err = reinterpret_cast<uint32_t *>(dctl.as<char>() + 68);
+            launch_useq(ctx, L);
+            IM_CUDA(cudaMemcpyAsync(h, dctl.p, 64, cudaMemcpyDeviceToHost, st));
+            uint32_t err = 0;
+            IM_CUDA(cudaMemcpyAsync(&err, dctl.as<char>() + 68, 4, cudaMemcpyDeviceToHost, st));
+            IM_CUDA(cudaStreamSynchronize(st));
+            if (err) fail(IMIN_ERANGE, "a world has more live edges inside its reach set than a slot holds");
+        }
+        if (credit_useq)
+            IM_CUDA(cudaMemcpyAsync(credit_useq, pcredit, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+        if (pcov) IM_CUDA(cudaMemcpyAsync(cov_world, pcov, (size_t)theta * 8, cudaMemcpyDeviceToHost, st));
+        IM_CUDA(cudaStreamSynchronize(st));
+        for (int i = 0; i < 5; ++i) totals[i] = h[i];
     });
 }
 

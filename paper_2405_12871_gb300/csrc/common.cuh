@@ -254,11 +254,39 @@ struct FTask {
     unsigned long long stop_T[3];    // per candidate: sizes still missing to its threshold
     unsigned long long *acc;         // [0..2] running sizes, [3] queue entries, [4] edges, [5] worlds
     uint32_t *sizes;                 // [count][4]: |R_j| per candidate (0 where not served)
+    uint32_t *deferred;              // relative indices of worlds that overflowed the queue
+    uint32_t *n_deferred;
+    uint32_t deferred_cap;
 };
-size_t final_slot_bytes(int32_t n, size_t *off_queue);
+size_t final_slot_bytes(int32_t n, int32_t qcap, size_t *off_queue);
 int final_blocks_per_sm(int bd);
-void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int bd, int ctas,
-                        void *slot_base, uint32_t *d_claim, uint32_t *d_done);
+void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int32_t qcap, int bd,
+                        int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
+
+// LRR sequences (useq_cta.cu): the LRR set of every reached node of every world.
+struct UseqLaunch {
+    const int32_t *row_ptr;
+    const uint4 *ce;
+    int32_t n;
+    const int32_t *S;
+    int32_t nS;
+    const uint32_t *seed_bm, *blocked_bm, *query_bm;   // blocked / query may be null
+    uint64_t key;
+    uint32_t tag, inst;
+    uint64_t first;
+    uint32_t count;
+    uint32_t *claim;              // zeroed world counter
+    void *slot_base;
+    int32_t ecap;                 // live-pair capacity of a slot
+    int ctas;
+    unsigned long long *credit;   // [n] or null
+    unsigned long long *cov_world;// [count] or null
+    unsigned long long *acc;      // [0] elements [1] coverage [2] nodes [3] edges [4] worlds
+    uint32_t *err;                // bit 4: a world's live pairs exceeded ecap
+};
+size_t useq_slot_bytes(int32_t n, int32_t ecap, size_t off[10]);
+int useq_blocks_per_sm();
+void launch_useq(imin_ctx *ctx, const UseqLaunch &L);
 
 // CTA-per-world reach kernel (reach_cta.cuh, sampler_cta.cu): the compiled shapes
 // {threads per CTA, CTAs per SM}

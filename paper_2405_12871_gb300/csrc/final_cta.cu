@@ -11,7 +11,10 @@
 // pre-marked with its bit, so they are never entered under it.  Each candidate's
 // reach set is therefore the one a separate traversal under its own blocked set would
 // find, and |R_j(B_c)| is the number of queue entries carrying bit c.  A node enters
-// the queue at most once per bit, so 3(n + 1) entries always suffice.
+// the queue at most once per bit, so 3(n + 1) entries always suffice; the host sizes
+// the queue from the expected spread instead, and a world that would overflow it is
+// abandoned (its slot's map wiped) and listed for the host, which runs it again one
+// candidate at a time.
 //
 // Stopping rule: worlds are claimed in index order.  A candidate whose running sum of
 // sizes has reached its threshold is dropped from the worlds claimed after that (its
@@ -38,6 +41,8 @@ struct FArgs {
     char *slot_base;
     size_t slot_bytes;
     size_t off_queue;
+    int32_t qcap;        // queue entries per slot
+    size_t nib_words;    // words of a slot's nibble map
     int l2_keep;
 };
 
@@ -45,7 +50,7 @@ struct FArgs {
 // candidate bits `om` and append the entries whose bits are new.  All lanes call it.
 __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int ob, int oe, uint32_t om,
                                            const Coins &K, uint32_t *nib, int32_t *Q, int *app, int tail,
-                                           int lane, uint32_t lt_mask)
+                                           int lane, uint32_t lt_mask, int qcap, int *ovf)
 {
     uint32_t live = 0;
     int4 c4 = make_int4(0, 0, 0, 0);
@@ -65,6 +70,10 @@ __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int 
     base = __shfl_sync(IMIN_FULL, base, 0);
     int pos = tail + base + __popc(b0 & lt_mask) + __popc(b1 & lt_mask) + __popc(b2 & lt_mask) +
               __popc(b3 & lt_mask);
+    if (tail + base + tot > qcap) {   // the queue is full: the world is abandoned
+        if (lane == 0) *ovf = 1;
+        return;
+    }
     if (n0) Q[pos++] = (c4.x << 3) | (int)n0;
     if (n1) Q[pos++] = (c4.y << 3) | (int)n1;
     if (n2) Q[pos++] = (c4.z << 3) | (int)n2;
@@ -76,7 +85,7 @@ __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int 
 // entries cut into pieces shared by the CTA.  Returns the final tail.
 template <int BD>
 __device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, uint32_t *nib, int32_t *Q, int tail0,
-                                         Shared<BD> &sh, unsigned long long &wedges)
+                                         Shared<BD> &sh, unsigned long long &wedges, int qcap, int *ovf)
 {
     const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -139,7 +148,7 @@ __device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, uint32_t
                 const int ox = __shfl_sync(IMIN_FULL, excl, pos);
                 const uint32_t om = (uint32_t)__shfl_sync(IMIN_FULL, x, pos) & 7u;
                 pass_multi(op, t < total, Fwd::first(ob) + (t - ox), ob, oe, om, K, nib, Q, &sh.app[p], tail,
-                           lane, lt_mask);
+                           lane, lt_mask, qcap, ovf);
             }
         }
         __syncthreads();
@@ -181,10 +190,11 @@ __device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, uint32_t
                 const int iend = min(i0 + PIECE, Fwd::first(ob) + Fwd::count(ob, oe));
                 for (int is = i0; is < iend; is += 32)
                     pass_multi(op, is + lane < iend, is + lane, ob, oe, om, K, nib, Q, &sh.app[p], tail, lane,
-                               lt_mask);
+                               lt_mask, qcap, ovf);
             }
         }
         __syncthreads();
+        if (*(volatile int *)ovf) return -1;   // entries were dropped: the world is abandoned
         const int ntail = tail + sh.app[p];
         head = tail;
         tail = ntail;
@@ -199,6 +209,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
     __shared__ Shared<BD> sh;
     __shared__ unsigned int cnt3[3];
     __shared__ uint32_t smask;
+    __shared__ int s_ovf;
 
     const int tid = threadIdx.x, lane = tid & 31;
     char *slot = a.slot_base + (size_t)blockIdx.x * a.slot_bytes;
@@ -236,6 +247,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
             sh.task = got;
             sh.rel = rel;
             smask = mask;
+            s_ovf = 0;
             sh.edges = 0;
             cnt3[0] = cnt3[1] = cnt3[2] = 0;
             sh.slice[0] = sh.nbig[0] = sh.piece[0] = sh.app[0] = 0;
@@ -270,7 +282,18 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
         __syncthreads();
         unsigned long long wedges = 0;
         const Fwd fwd{T.row_ptr, T.ce, reach_cta::graph_l2_policy(a.l2_keep != 0)};
-        const int tail = bfs_multi<BD>(fwd, K, nib, Q, nS, sh, wedges);
+        const int tail = bfs_multi<BD>(fwd, K, nib, Q, nS, sh, wedges, a.qcap, &s_ovf);
+        if (tail < 0) {
+            // overflow: wipe the map (dropped entries left bits that the queue cannot
+            // find) and list the world for the host
+            for (size_t w = tid; w < a.nib_words; w += BD) nib[w] = 0u;
+            if (tid == 0) {
+                const uint32_t d = atomicAdd(T.n_deferred, 1u);
+                if (d < T.deferred_cap) T.deferred[d] = rel;
+            }
+            __syncthreads();
+            continue;
+        }
 
         // ---- per-candidate sizes; the nibble map is cleared through the queue ----
         unsigned int c0 = 0, c1 = 0, c2 = 0;
@@ -325,16 +348,16 @@ namespace {
 inline size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 }  // namespace
 
-// slot: [nibble map: 4 bits per node] [queue: 3 (n + 1) packed entries]
-size_t final_slot_bytes(int32_t n, size_t *off_queue)
+// slot: [nibble map: 4 bits per node] [queue: qcap packed entries]
+size_t final_slot_bytes(int32_t n, int32_t qcap, size_t *off_queue)
 {
     const size_t nib = al256((((size_t)n + 7) / 8) * 4);
     if (off_queue) *off_queue = nib;
-    return nib + al256(3 * ((size_t)n + 1) * 4);
+    return nib + al256((size_t)qcap * 4);
 }
 
-void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int bd, int ctas,
-                        void *slot_base, uint32_t *d_claim, uint32_t *d_done)
+void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int32_t qcap, int bd,
+                        int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done)
 {
     final_cta::FArgs a;
     a.tasks = d_tasks;
@@ -342,7 +365,9 @@ void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t
     a.claim = d_claim;
     a.done = d_done;
     a.slot_base = reinterpret_cast<char *>(slot_base);
-    a.slot_bytes = final_slot_bytes(nmax, &a.off_queue);
+    a.slot_bytes = final_slot_bytes(nmax, qcap, &a.off_queue);
+    a.qcap = qcap;
+    a.nib_words = ((size_t)nmax + 7) / 8;
     const char *env = std::getenv("IMIN_L2_KEEP");
     a.l2_keep = (env && env[0] == '0') ? 0 : 1;
     if (bd == 256)

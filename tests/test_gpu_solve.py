@@ -195,8 +195,8 @@ def test_controller_pin_graphs(ctx, which):
     G.free()
 
 
-@pytest.mark.parametrize("chunk", [None, "613"])
-def test_final_estimates_fused_and_separate(ctx, monkeypatch, chunk):
+@pytest.mark.parametrize("chunk,qcap", [(None, None), ("613", None), (None, "400")])
+def test_final_estimates_fused_and_separate(ctx, monkeypatch, chunk, qcap):
     """The final estimates of the three candidates run as one traversal per world with a
     per-node candidate mask; one stopping rule per candidate on the same worlds gives
     the same N and estimates, and both equal the oracle's (also in many small chunks)."""
@@ -206,6 +206,8 @@ def test_final_estimates_fused_and_separate(ctx, monkeypatch, chunk):
     kw = dict(k=15, eps=0.3, delta=1.0 / g.n, key=4)
     if chunk:
         monkeypatch.setenv("IMIN_STOP_CHUNK", chunk)
+    if qcap:
+        monkeypatch.setenv("IMIN_FINAL_QCAP", qcap)
     G = ctx.load_graph(g)
     fused = G.solve(S, **kw)
     monkeypatch.setenv("IMIN_FINAL_FUSED", "0")
@@ -215,3 +217,25 @@ def test_final_estimates_fused_and_separate(ctx, monkeypatch, chunk):
     compare(fused, separate)
     compare(fused, og.solve(S, **kw))
     assert len(set(fused["n_final"])) > 1      # each candidate stops at its own N
+
+
+@pytest.mark.parametrize("qcap", [None, "300"])
+def test_final_estimates_entry_point(ctx, monkeypatch, qcap):
+    """imin_final_estimates on given blocker sets equals the oracle's stopping rule for
+    each set on the worlds of tag 5; with a 300-entry queue most worlds overflow the
+    fused traversal and are re-run one candidate at a time, with the same results."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=7)
+    S = synth.seeds_top_outdeg(g, 12, 0.01, seed=8)
+    og = oracle.OracleGraph.from_graph(g)
+    rng = np.random.default_rng(5)
+    pool = np.setdiff1d(np.arange(g.n), S)
+    cands = [np.sort(rng.choice(pool, k, replace=False)) for k in (10, 25, 0)]
+    if qcap:
+        monkeypatch.setenv("IMIN_FINAL_QCAP", qcap)
+    G = ctx.load_graph(g)
+    for nc in (3, 2, 1):
+        I, N = G.final_estimates(S, cands[:nc], gamma=0.1, delta=1.0 / g.n, key=6, inst=2, spread_hint=50.0)
+        for c in range(nc):
+            wN, wI = og.stop_rule(S, cands[c], beta=0.1, dprime=1.0 / g.n, key=6, tag=5, inst=2)
+            assert (N[c], I[c]) == (wN, wI), (nc, c)
+    G.free()
