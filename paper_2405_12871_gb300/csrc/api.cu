@@ -267,6 +267,19 @@ struct Runner {
                 c.cta_minb = gref->tuned_minb;
                 c.qcap = n + 1;
                 c.ctas = gref->tuned_ctas;
+                if (c.lower) {
+                    // lower-bound worlds (dominators: many barriers per world) run on
+                    // 512-thread CTAs, 4 per SM, whatever the reach-only tuning chose
+                    // (IMIN_LOWER_BD=256/512/1024 selects another CTA size)
+                    int lbd = 512;
+                    if (const char *env = std::getenv("IMIN_LOWER_BD")) {
+                        const long v = std::strtol(env, nullptr, 10);
+                        if (v == 256 || v == 512 || v == 1024) lbd = (int)v;
+                    }
+                    c.cta_threads = lbd;
+                    c.cta_minb = lbd == 256 ? 8 : (lbd == 512 ? 4 : 2);
+                    c.ctas = ctx->num_sms * c.cta_minb;
+                }
                 if (c.lower || c.upper) {
                     // the same shape, at most as many CTAs per SM as the bound's kernel fits
                     if (c.smem_bm) {
@@ -863,8 +876,9 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
     }
     const int occ = std::max(1, std::min(minb, final_blocks_per_sm(bd)));
     // queue entries per slot: a world needs at most the three reach sets' sizes; the
-    // queue holds 8 times the expected spread (all 3 (n + 1) when it is not known), and
-    // a world that overflows it is re-run one candidate at a time below
+    // queue holds 32 times the expected spread (all 3 (n + 1) when it is not known), and
+    // a world that overflows it (the reach distribution has a long tail) is re-run one
+    // candidate at a time below
     double hint = 0.0;
     int32_t nSmax = 1;
     for (const FinalSpec &f : specs) {
@@ -872,7 +886,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         nSmax = std::max<int32_t>(nSmax, (int32_t)f.q->S.size());
     }
     const double full = 3.0 * ((double)nmax + 1.0);
-    int32_t qcap = (int32_t)std::min(full, std::max(65536.0, 8.0 * hint + 3.0 * nSmax));
+    int32_t qcap = (int32_t)std::min(full, std::max(262144.0, 32.0 * hint + 3.0 * nSmax));
     if (const char *qe = std::getenv("IMIN_FINAL_QCAP")) {   // test hook: tiny queues, many re-runs
         const long v = std::strtol(qe, nullptr, 10);
         if (v > nSmax && v < qcap) qcap = (int32_t)v;
@@ -974,6 +988,20 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         std::vector<uint32_t> claims(nt);
         IM_CUDA(cudaMemcpy(acc.data(), ctl.p, acc.size() * 8, cudaMemcpyDeviceToHost));
         IM_CUDA(cudaMemcpy(claims.data(), cd.p, (size_t)nt * 4, cudaMemcpyDeviceToHost));
+        if (const char *tr = std::getenv("IMIN_TRACE"))
+            if (tr[0] == '1') {
+                unsigned long long w = 0, en = 0, ed = 0, nd = 0;
+                for (int k = 0; k < nt; ++k) {
+                    en += acc[(size_t)k * 8 + 3];
+                    ed += acc[(size_t)k * 8 + 4];
+                    w += acc[(size_t)k * 8 + 5];
+                    nd += (uint32_t)acc[(size_t)k * 8 + 6];
+                }
+                std::fprintf(stderr,
+                             "[imin] fused final launch: %d task(s), %llu worlds, %llu queue entries, %llu edges, "
+                             "%llu overflowed, %.3f ms, %zu CTAs x %d threads, queue %d\n",
+                             nt, w, en, ed, nd, ms, ctas, bd, qcap);
+            }
         // worlds that overflowed the fused queue: each candidate's size by its own
         // reach-only traversal of the same world (tag 5), all in one launch
         {
