@@ -1282,6 +1282,110 @@ void sample_lrr(imin_ctx *ctx, std::vector<LrrJob> &jobs)
         tp.push_back(&t);
     }
     if (tp.empty()) return;
+    const char *rev_env = std::getenv("IMIN_GS_REVERSE");
+    double rev_ms = 0.0;
+    uint64_t rev_launches = 0;
+    if (!(rev_env && rev_env[0] == '0')) {
+        // Global Sampling worlds backwards from the target (gs_rev.cu); the worlds it
+        // leaves (reverse set too large, or no store room) run forwards below
+        const int nt = (int)tp.size();
+        DBuf ctl, cd, dt, defl;
+        ctl.ensure(ctx, (size_t)nt * CTL);
+        IM_CUDA(cudaMemsetAsync(ctl.p, 0, (size_t)nt * CTL, ctx->stream));
+        size_t tot = 0;
+        for (TaskRun *t : tp) tot += t->count;
+        defl.ensure(ctx, tot * 4 + 16);
+        std::vector<WTask> ht;
+        size_t at = 0;
+        char *c0 = reinterpret_cast<char *>(ctl.p);
+        for (int i = 0; i < nt; ++i) {
+            WorldOut o = tp[i]->out;
+            o.acc = reinterpret_cast<unsigned long long *>(c0 + (size_t)i * CTL);
+            o.n_deferred = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 64);
+            o.err = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 68);
+            o.deferred = defl.as<uint32_t>() + at;
+            o.deferred_cap = tp[i]->count;
+            at += tp[i]->count;
+            ht.push_back(make_task(tp[i]->g, tp[i]->q, tp[i]->first, tp[i]->count, nullptr, o));
+        }
+        dt.ensure(ctx, ht.size() * sizeof(WTask));
+        cd.ensure(ctx, (size_t)nt * 8 + 16);
+        IM_CUDA(cudaMemcpyAsync(dt.p, ht.data(), ht.size() * sizeof(WTask), cudaMemcpyHostToDevice, ctx->stream));
+        IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)nt * 8, ctx->stream));
+        EventTimer et(ctx);
+        launch_gs_rev(ctx, dt.as<WTask>(), nt, cd.as<uint32_t>(), cd.as<uint32_t>() + nt);
+        rev_ms = et.stop();
+        rev_launches = 1;
+        std::vector<unsigned char> hc((size_t)nt * CTL);
+        IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));
+        uint32_t e = 0;
+        for (int i = 0; i < nt; ++i) {
+            uint32_t x;
+            std::memcpy(&x, hc.data() + (size_t)i * CTL + 68, 4);
+            e |= x;
+        }
+        if (e) fail(IMIN_EDEVICE, "device invariant failed (reverse Global Sampling)");
+        // the worlds left over, as lists of world offsets for the forward kernel
+        std::vector<std::vector<uint32_t>> left(nt);
+        size_t nleft = 0;
+        at = 0;
+        for (int i = 0; i < nt; ++i) {
+            uint32_t nd = 0;
+            std::memcpy(&nd, hc.data() + (size_t)i * CTL + 64, 4);
+            std::memcpy(tp[i]->acc, hc.data() + (size_t)i * CTL, 64);
+            if (nd) {
+                left[i].resize(nd);
+                IM_CUDA(cudaMemcpy(left[i].data(), defl.as<uint32_t>() + at, (size_t)nd * 4, cudaMemcpyDeviceToHost));
+                for (uint32_t &x : left[i]) x &= 0x7fffffffu;
+                std::sort(left[i].begin(), left[i].end());
+                nleft += nd;
+            }
+            at += tp[i]->count;
+        }
+        std::vector<TaskRun *> keep;
+        DBuf dleft;
+        if (nleft) {
+            dleft.ensure(ctx, nleft * 4 + 16);
+            size_t o = 0;
+            for (int i = 0; i < nt; ++i) {
+                if (left[i].empty()) continue;
+                IM_CUDA(cudaMemcpy(dleft.as<uint32_t>() + o, left[i].data(), left[i].size() * 4, cudaMemcpyHostToDevice));
+                tp[i]->list = dleft.as<uint32_t>() + o;
+                tp[i]->count = (uint32_t)left[i].size();
+                o += left[i].size();
+                keep.push_back(tp[i]);
+            }
+        }
+        std::vector<std::array<unsigned long long, 8>> acc_rev(nt);
+        for (int i = 0; i < nt; ++i) std::memcpy(acc_rev[i].data(), tp[i]->acc, 64);
+        if (!keep.empty()) {
+            Runner run(ctx);
+            run.run(keep, WF_UPPER | WF_STORE);
+            rev_ms += run.kernel_ms;
+            rev_launches += (uint64_t)run.launches;
+        }
+        for (int i = 0; i < nt; ++i) {
+            const bool rerun = !left[i].empty();
+            for (int k = 0; k < 8; ++k) tp[i]->acc[k] = acc_rev[i][k] + (rerun ? tp[i]->acc[k] : 0ull);
+        }
+        for (size_t i = 0; i < nj; ++i) {
+            LrrJob &J = jobs[i];
+            if (J.to <= J.from) continue;
+            LrrStore &L = *J.L;
+            unsigned long long used = 0;
+            IM_CUDA(cudaMemcpy(&used, L.cursor.p, 8, cudaMemcpyDeviceToHost));
+            L.elems = used;
+            L.nsets = (uint32_t)J.to;
+            if (J.stats) {
+                J.stats->worlds += tr[i].acc[4];
+                J.stats->edges += tr[i].acc[1];
+                J.stats->nodes += tr[i].acc[0];
+                J.stats->kernel_ms += rev_ms / (double)tp.size();
+                J.stats->launches += rev_launches;
+            }
+        }
+        return;
+    }
     Runner run(ctx);
     run.run(tp, WF_UPPER | WF_STORE);
     for (size_t i = 0; i < nj; ++i) {
