@@ -250,7 +250,11 @@ def run_batch(args):
     Gs = [ctx.load_graph(g) for g, _, _ in items]
     qs = [(G, S, c["k"], c["eps"], c["delta"], dict(key=c["key"], inst=c["inst"]))
           for G, (g, S, c) in zip(Gs, items)]
-    # warm-up on a small instance (loads the kernels, sizes the slot arenas)
+    # warm-up: every graph's launch shape is tuned before either path is timed (the
+    # autotuner otherwise runs inside the first solve that reaches a graph), and a
+    # small instance loads the kernels and sizes the slot arenas
+    for (G, S, k, eps, delta, kw) in qs:
+        G.autotune(S)
     small = min(range(len(items)), key=lambda i: items[i][0].n)
     G, S, k, eps, delta, kw = qs[small]
     G.solve(S, k, eps, delta, **kw)
@@ -275,6 +279,9 @@ def run_batch(args):
             "total_nodes": int(sum(g.n for g, _, _ in items)),
             "total_edges": int(sum(g.m for g, _, _ in items)),
             "batched_kernel_launches": int(batched[0]["kernel_launches"]),
+            "batched_stage_ms": [round(x, 1) for x in batched[0]["ms_stage"]],
+            "batched_kernel_ms": [round(x, 1) for x in batched[0]["kernel_ms"]],
+            "plain_stage_ms_sum": [round(sum(x["ms_stage"][i] for x in plain), 1) for i in range(8)],
             "plain_kernel_launches": int(sum(x["kernel_launches"] for x in plain)),
             "config": {"workload": "batch of Chung-Lu instances", "n": "log-uniform 1e3..1e6",
                        "avg_degree": 10, "exponent": 2.1, "seeds": "U{5..100} from top-1% out-degree",
@@ -366,6 +373,8 @@ def run_serve(args):
     Gs = [ctx.load_graph(g) for g in graphs]
     nq = int(rng.poisson(args.serve_rate * args.serve_seconds))
     arrivals = np.sort(rng.uniform(0.0, args.serve_seconds, size=nq))
+    if args.serve_burst:            # every query arrives at once: throughput at saturation
+        arrivals = np.zeros(nq)
     qs = []
     for i in range(nq):
         gi = int(rng.integers(0, len(graphs)))
@@ -374,10 +383,13 @@ def run_serve(args):
         S = np.sort(rng.choice(g.n, nS, replace=False)).astype(np.int32)
         k = int(min(rng.integers(10, 501), g.n - nS - 1))
         qs.append((Gs[gi], S, k, 0.2, 1.0 / g.n, dict(key=i, inst=i)))
-    # warm-up
+    # warm-up: the three graphs' launch shapes are tuned before either path is timed
+    for G in Gs:
+        seeds = next((q[1] for q in qs if q[0] is G), np.arange(10, dtype=np.int32))
+        G.autotune(seeds)
     G, S, k, eps, delta, kw = qs[0]
     G.solve(S, k, eps, delta, **kw)
-    srv = _lib.Server(ctx, max_active=32)
+    srv = _lib.Server(ctx, max_active=args.serve_active)
     t0 = time.perf_counter()
     tickets = []
     for (G, S, k, eps, delta, kw), at in zip(qs, arrivals):
@@ -403,14 +415,14 @@ def run_serve(args):
         lat_p.append(free_at - at)
     lat_p = np.array(lat_p)
     same = all(list(x["blockers"]) == list(y["blockers"]) for x, y in zip(plain, served))
-    line = {"mode": "serve", "queries": nq, "rate_per_s": args.serve_rate,
+    line = {"mode": "serve", "queries": nq, "rate_per_s": args.serve_rate, "burst": bool(args.serve_burst),
             "duration_s": args.serve_seconds, "served_qps": nq / t_served,
             "served_p50_s": float(np.percentile(lat_s, 50)), "served_p99_s": float(np.percentile(lat_s, 99)),
             "plain_qps": nq / float(np.sum(service)), "plain_p50_s": float(np.percentile(lat_p, 50)),
             "plain_p99_s": float(np.percentile(lat_p, 99)), "identical_results": same,
             "config": {"graphs": "Chung-Lu (Poisson model) 1e5 / 3e5 / 1e6 nodes, degree 10, WC p",
                        "arrivals": "Poisson", "seeds": "U{10..200} uniform nodes", "k": "U{10..500}",
-                       "eps": 0.2, "delta": "1/n", "max_active": 32}}
+                       "eps": 0.2, "delta": "1/n", "max_active": args.serve_active}}
     print(json.dumps(line), flush=True)
     for G in Gs:
         G.free()
@@ -578,6 +590,9 @@ def main():
                          "continuous-batching server vs a plain one-at-a-time replay")
     ap.add_argument("--serve-rate", type=float, default=4.0)
     ap.add_argument("--serve-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-active", type=int, default=32)
+    ap.add_argument("--serve-burst", action="store_true",
+                    help="all queries of the stream arrive at time 0 (throughput at saturation)")
     ap.add_argument("--sweep", action="store_true",
                     help="eps / |S| / k sweeps of the solve on the CL-1M stand-in")
     ap.add_argument("--baselines", action="store_true",

@@ -103,6 +103,14 @@ int imin_load_graph(imin_ctx *ctx, int32_t n, int64_t m, const int32_t *row_ptr,
 /* Release a graph.  NULL is ignored. */
 void imin_free_graph(imin_graph *g);
 
+/* Choose the reach-only launch shape of graph g now (the autotuner otherwise runs on
+ * the first stopping-rule estimate that reaches the graph): every compiled CTA shape
+ * and the warp-per-world kernel are timed on worlds from the seeds S (a stream no
+ * solve draws; no result changes), and the fastest is kept for g and for every graph
+ * of the same shape in the context.  A graph that is already tuned is left as it is.
+ * Errors: IMIN_EINVAL, IMIN_ENOMEM, IMIN_EDEVICE. */
+int imin_graph_autotune(imin_graph *g, const int32_t *S, int32_t nS);
+
 /* The launch configuration the library's autotuner chose for reach-only worlds on
  * this graph (performance only: every configuration gives the same counts).  The
  * first stopping-rule estimate on a graph times a short probe of each configuration

@@ -20,7 +20,7 @@ VARIANTS = {"sandimin": 0, "sandimin-": 1, "lsbm": 2, "gsbm": 3, "lhga": 4}
 # names the library must export (checked by the CPU tests against include/imin.h)
 EXPORTS = ["imin_create", "imin_destroy", "imin_load_graph", "imin_free_graph", "imin_sample",
            "imin_solve", "imin_strerror", "imin_last_error", "imin_sample_reach_noalloc",
-           "imin_sample_lrr_sequences", "imin_final_estimates",
+           "imin_sample_lrr_sequences", "imin_final_estimates", "imin_graph_autotune",
            "imin_solve_batch", "imin_server_start", "imin_server_submit", "imin_server_poll",
            "imin_server_stop", "imin_graph_tuning"]
 NOALLOC_MAX_NODES = 2_000_000
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = True):
     L.imin_load_graph.restype = C.c_int
     L.imin_free_graph.argtypes = [C.c_void_p]
     L.imin_free_graph.restype = None
+    L.imin_graph_autotune.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32]
+    L.imin_graph_autotune.restype = C.c_int
     L.imin_graph_tuning.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.imin_graph_tuning.restype = C.c_int
     L.imin_sample.argtypes = [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_int32), C.c_int32,
@@ -376,6 +378,11 @@ class Graph:
         if per_world:
             out["cov_world"] = cw[: int(theta)]
         return out
+
+    def autotune(self, S):
+        """imin_graph_autotune: choose the reach-only launch shape now."""
+        S = _as_i32(S)
+        _check(self.ctx.h, load().imin_graph_autotune(self.h, _i32p(S), len(S)), "imin_graph_autotune")
 
     def tuning(self):
         """The autotuner's reach-only launch choice: dict(ctas, threads, minb, smem_bitmap)."""

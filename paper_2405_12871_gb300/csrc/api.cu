@@ -671,7 +671,7 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
     std::vector<double> W(ns), ups1(ns);
     std::vector<unsigned long long> T(ns), sum(ns, 0);
     std::vector<uint64_t> first(ns, 0), N(ns, 0), chunk(ns);
-    std::vector<DBuf> spread(ns);
+    std::vector<size_t> soff(ns, 0);   // per estimate: offset of its sizes in ctx->stop_spread
     for (size_t i = 0; i < ns; ++i) {
         StopSpec &sp = specs[i];
         W[i] = (double)sp.q->nVs + (double)sp.q->S.size();
@@ -697,16 +697,24 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
         std::vector<TaskRun> tr(ns);
         std::vector<TaskRun *> tp;
         std::vector<size_t> idx;
+        // the per-world sizes of every estimate of this launch, in one cached buffer
+        size_t total = 0;
         for (size_t i = 0; i < ns; ++i) {
             if (N[i]) continue;
             const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
-            spread[i].ensure(ctx, (size_t)cnt * 4 + 16);
+            soff[i] = total;
+            total += ((size_t)cnt + 4) & ~(size_t)3;
+        }
+        ctx->stop_spread.ensure(ctx, total * 4 + 16);
+        for (size_t i = 0; i < ns; ++i) {
+            if (N[i]) continue;
+            const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
             TaskRun &t = tr[i];
             t.g = specs[i].g;
             t.q = qdev(*specs[i].q, specs[i].key, specs[i].tag, specs[i].inst);
             t.first = first[i];
             t.count = (uint32_t)cnt;
-            t.out.world_spread = spread[i].as<uint32_t>();
+            t.out.world_spread = ctx->stop_spread.as<uint32_t>() + soff[i];
             t.out.stop_T = T[i] - sum[i];
             tp.push_back(&t);
             idx.push_back(i);
@@ -737,7 +745,9 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
             // every claimed world is complete (deferred ones were re-run)
             const uint64_t want = tr[i].claimed_main;
             std::vector<uint32_t> sizes(want);
-            if (want) IM_CUDA(cudaMemcpy(sizes.data(), spread[i].p, want * 4, cudaMemcpyDeviceToHost));
+            if (want)
+                IM_CUDA(cudaMemcpy(sizes.data(), ctx->stop_spread.as<uint32_t>() + soff[i], want * 4,
+                                   cudaMemcpyDeviceToHost));
             for (uint64_t j = 0; j < want; ++j) {
                 sum[i] += sizes[j];
                 if (sum[i] >= T[i]) {
@@ -862,10 +872,11 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
     }
     // launch shape: the graph's tuned CTA size (256 or 512 threads), as many CTAs as are
     // resident, within half of the free memory
+    // 256 threads x 8 CTAs per SM (the fastest shape of this kernel on the power-law
+    // workloads measured; the reach-only tuning does not carry over: the candidate map
+    // is four times the visited bitmap)
     int bd = 256;
-    for (const FinalSpec &f : specs)
-        if (f.g->tuned_ctas > 0 && f.g->tuned_bd >= 512) bd = 512;
-    int minb = bd == 256 ? 8 : 4;
+    int minb = 8;
     // tuning hook: IMIN_FINAL_SHAPE=<threads>:<CTAs per SM> (256 or 512 threads)
     if (const char *fe = std::getenv("IMIN_FINAL_SHAPE")) {
         int b = 0, m = 0;
@@ -902,7 +913,9 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
     if (per * ctas > avail) ctas = std::max<size_t>(avail / per, 1);
     if (per > freeb) fail(IMIN_ENOMEM, "not enough device memory for the final estimates");
     DBuf ctl, cd, dtasks, rerun_ws;
-    std::vector<DBuf> sizes(ns), defl(ns);
+    // per spec and launch: sizes [count][4] and the overflow list, in one cached buffer
+    std::vector<size_t> zoff(ns, 0), doff(ns, 0);
+
     std::vector<std::vector<uint32_t>> hsz(ns);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     IM_CUDA(cudaEventCreate(&e0));
@@ -918,6 +931,20 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
     for (;;) {
         std::vector<FTask> ht;
         std::vector<size_t> idx;
+        size_t total = 0;
+        for (size_t i = 0; i < ns; ++i) {
+            bool any = false;
+            for (int c = 0; c < 3; ++c) any |= specs[i].use[c] && !N[i][c];
+            if (!any) continue;
+            const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
+            zoff[i] = total;
+            total += (size_t)cnt * 4 + 4;
+            doff[i] = total;
+            total += ((size_t)cnt + 4) & ~(size_t)3;
+        }
+        ctx->final_scratch.ensure(ctx, total * 4 + 16);
+        auto sizes_of = [&](size_t i) { return ctx->final_scratch.as<uint32_t>() + zoff[i]; };
+        auto defl_of = [&](size_t i) { return ctx->final_scratch.as<uint32_t>() + doff[i]; };
         for (size_t i = 0; i < ns; ++i) {
             FinalSpec &f = specs[i];
             uint32_t cands = 0;
@@ -925,7 +952,6 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
                 if (f.use[c] && !N[i][c]) cands |= 1u << c;
             if (!cands) continue;
             const uint64_t cnt = std::min<uint64_t>(chunk[i], ((uint64_t)1 << 32) - 1 - first[i]);
-            sizes[i].ensure(ctx, (size_t)cnt * 16 + 16);
             FTask t{};
             t.row_ptr = f.g->row_ptr.as<int32_t>();
             t.ce = f.g->ce.as<uint4>();
@@ -942,9 +968,8 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
             t.inst = f.inst;
             t.first = first[i];
             t.count = (uint32_t)cnt;
-            t.sizes = sizes[i].as<uint32_t>();
-            defl[i].ensure(ctx, (size_t)cnt * 4 + 16);
-            t.deferred = defl[i].as<uint32_t>();
+            t.sizes = sizes_of(i);
+            t.deferred = defl_of(i);
             t.deferred_cap = (uint32_t)cnt;
             ht.push_back(t);
             idx.push_back(i);
@@ -1028,7 +1053,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
                         t.q = qdev(*specs[i].qb[c], specs[i].key, TAG_FINAL, specs[i].inst);
                         t.first = ht[k].first;
                         t.count = nd[k];
-                        t.list = defl[i].as<uint32_t>();
+                        t.list = defl_of(i);
                         t.out.world_spread = rerun_ws.as<uint32_t>() + at;
                         at += ht[k].count;
                         rr.push_back(t);
@@ -1048,12 +1073,12 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
                     const int k = rref[r].first, c = rref[r].second;
                     const size_t i = idx[k];
                     hdef.resize(nd[k]);
-                    IM_CUDA(cudaMemcpy(hdef.data(), defl[i].p, (size_t)nd[k] * 4, cudaMemcpyDeviceToHost));
+                    IM_CUDA(cudaMemcpy(hdef.data(), defl_of(i), (size_t)nd[k] * 4, cudaMemcpyDeviceToHost));
                     // the re-run's sizes sit at the worlds' relative indices
                     std::vector<uint32_t> szk((size_t)ht[k].count * 4);
-                    IM_CUDA(cudaMemcpy(szk.data(), sizes[i].p, szk.size() * 4, cudaMemcpyDeviceToHost));
+                    IM_CUDA(cudaMemcpy(szk.data(), sizes_of(i), szk.size() * 4, cudaMemcpyDeviceToHost));
                     for (uint32_t rel : hdef) szk[(size_t)rel * 4 + c] = hws[at + rel];
-                    IM_CUDA(cudaMemcpy(sizes[i].p, szk.data(), szk.size() * 4, cudaMemcpyHostToDevice));
+                    IM_CUDA(cudaMemcpy(sizes_of(i), szk.data(), szk.size() * 4, cudaMemcpyHostToDevice));
                     SpreadEst &r0 = specs[i].est[c];
                     r0.nodes += rr[r].acc[0];
                     r0.edges += rr[r].acc[1];
@@ -1067,7 +1092,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
             FinalSpec &f = specs[i];
             const uint64_t got = std::min<uint64_t>(claims[k], ht[k].count);
             hsz[i].resize(got * 4);
-            if (got) IM_CUDA(cudaMemcpy(hsz[i].data(), sizes[i].p, got * 16, cudaMemcpyDeviceToHost));
+            if (got) IM_CUDA(cudaMemcpy(hsz[i].data(), sizes_of(i), got * 16, cudaMemcpyDeviceToHost));
             // launch totals are shared by the candidates: the first served one gets them
             int first_c = -1;
             for (int c = 0; c < 3; ++c) {
@@ -2057,6 +2082,10 @@ void imin_destroy(imin_ctx *ctx)
     ctx->slots_lower.release();
     ctx->big_slots.release();
     ctx->slots_final.release();
+    ctx->stop_spread.release();
+    ctx->final_scratch.release();
+    for (DBuf *b : {&ctx->vs_vis, &ctx->vs_qa, &ctx->vs_qb, &ctx->vs_hubs, &ctx->vs_ctl, &ctx->vs_cnt, &ctx->vs_tmp})
+        b->release();
     ctx->misc.release();
     delete ctx;
 }
@@ -2109,6 +2138,18 @@ void imin_free_graph(imin_graph *g)
     if (!g) return;
     cudaSetDevice(g->ctx->device);
     delete g;
+}
+
+int imin_graph_autotune(imin_graph *g, const int32_t *S, int32_t nS)
+{
+    if (!g) return IMIN_EINVAL;
+    imin_ctx *ctx = g->ctx;
+    return run_guarded(ctx, [&] {
+        IM_CUDA(cudaSetDevice(ctx->device));
+        Query q;
+        prepare_query(ctx, g, q, S, nS, nullptr, 0, false);
+        autotune_reach(ctx, g, q);
+    });
 }
 
 int imin_graph_tuning(const imin_graph *g, int32_t out[4])

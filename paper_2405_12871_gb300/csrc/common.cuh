@@ -125,6 +125,9 @@ struct imin_ctx {
     };
     std::vector<TuneEntry> tune_cache;
     DBuf misc;              // small per-call device scalars
+    DBuf vs_vis, vs_qa, vs_qb, vs_hubs, vs_ctl, vs_cnt, vs_tmp;   // V'_s search work buffers
+    DBuf stop_spread;       // per-world sizes of the stopping-rule launches
+    DBuf final_scratch;     // per-world candidate sizes and overflow lists of the fused finals
     DBuf hostpin_dummy;
     unsigned long long *h_misc = nullptr;  // pinned host mirror of `misc` scalars
 };

@@ -239,3 +239,20 @@ def test_final_estimates_entry_point(ctx, monkeypatch, qcap):
             wN, wI = og.stop_rule(S, cands[c], beta=0.1, dprime=1.0 / g.n, key=6, tag=5, inst=2)
             assert (N[c], I[c]) == (wN, wI), (nc, c)
     G.free()
+
+
+def test_explicit_autotune_changes_nothing(ctx):
+    """imin_graph_autotune picks the launch shape up front; a solve afterwards gives the
+    same bits as one that tunes on its own first estimate."""
+    g = synth.chung_lu(20_000, 10.0, 2.1, seed=5)
+    S = synth.seeds_top_outdeg(g, 15, 0.01, seed=6)
+    kw = dict(k=6, eps=0.3, delta=0.05, key=2)
+    G = ctx.load_graph(g)
+    assert G.tuning()["ctas"] == 0
+    G.autotune(S)
+    t = G.tuning()
+    assert t["ctas"] != 0
+    a = G.solve(S, **kw)
+    assert G.tuning() == t
+    G.free()
+    compare(a, oracle.OracleGraph.from_graph(g).solve(S, **kw))
