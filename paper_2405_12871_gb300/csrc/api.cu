@@ -1311,62 +1311,115 @@ void sample_lrr(imin_ctx *ctx, std::vector<LrrJob> &jobs)
     double rev_ms = 0.0;
     uint64_t rev_launches = 0;
     if (!(rev_env && rev_env[0] == '0')) {
-        // Global Sampling worlds backwards from the target (gs_rev.cu); the worlds it
-        // leaves (reverse set too large, or no store room) run forwards below
+        // Global Sampling worlds backwards from the target (gs_rev.cu): every world with
+        // the narrow per-warp tables, the few it cannot hold with the wide ones, and
+        // what is left (reverse set still too large, or no store room) forwards below
         const int nt = (int)tp.size();
-        DBuf ctl, cd, dt, defl;
-        ctl.ensure(ctx, (size_t)nt * CTL);
-        IM_CUDA(cudaMemsetAsync(ctl.p, 0, (size_t)nt * CTL, ctx->stream));
-        size_t tot = 0;
-        for (TaskRun *t : tp) tot += t->count;
-        defl.ensure(ctx, tot * 4 + 16);
-        std::vector<WTask> ht;
-        size_t at = 0;
-        char *c0 = reinterpret_cast<char *>(ctl.p);
-        for (int i = 0; i < nt; ++i) {
-            WorldOut o = tp[i]->out;
-            o.acc = reinterpret_cast<unsigned long long *>(c0 + (size_t)i * CTL);
-            o.n_deferred = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 64);
-            o.err = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 68);
-            o.deferred = defl.as<uint32_t>() + at;
-            o.deferred_cap = tp[i]->count;
-            at += tp[i]->count;
-            ht.push_back(make_task(tp[i]->g, tp[i]->q, tp[i]->first, tp[i]->count, nullptr, o));
+        // one reverse pass over the worlds lists[i] of task i (all of them when
+        // `all`); adds its counters to acc[i] and returns the worlds it leaves, split
+        // into too-large (big) and no-store-room (small)
+        std::vector<std::array<unsigned long long, 8>> acc_rev(nt);
+        for (auto &a8 : acc_rev) a8.fill(0ull);
+        auto rev_pass = [&](bool wide, const std::vector<std::vector<uint32_t>> *lists,
+                            std::vector<std::vector<uint32_t>> &big, std::vector<std::vector<uint32_t>> &small) {
+            DBuf ctl, cd, dt, defl, dl;
+            ctl.ensure(ctx, (size_t)nt * CTL);
+            IM_CUDA(cudaMemsetAsync(ctl.p, 0, (size_t)nt * CTL, ctx->stream));
+            size_t tot = 0, ltot = 0;
+            for (int i = 0; i < nt; ++i) {
+                tot += tp[i]->count;
+                if (lists) ltot += (*lists)[i].size();
+            }
+            defl.ensure(ctx, tot * 4 + 16);
+            if (lists) dl.ensure(ctx, ltot * 4 + 16);
+            std::vector<WTask> ht;
+            std::vector<int> owner;
+            size_t at = 0, lat = 0;
+            char *c0 = reinterpret_cast<char *>(ctl.p);
+            int maxw = 0;
+            for (int i = 0; i < nt; ++i) {
+                const uint32_t cnt = lists ? (uint32_t)(*lists)[i].size() : tp[i]->count;
+                WorldOut o = tp[i]->out;
+                o.acc = reinterpret_cast<unsigned long long *>(c0 + (size_t)i * CTL);
+                o.n_deferred = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 64);
+                o.err = reinterpret_cast<uint32_t *>(c0 + (size_t)i * CTL + 68);
+                o.deferred = defl.as<uint32_t>() + at;
+                o.deferred_cap = tp[i]->count;
+                at += tp[i]->count;
+                if (cnt == 0) continue;
+                const uint32_t *list = nullptr;
+                if (lists) {
+                    IM_CUDA(cudaMemcpy(dl.as<uint32_t>() + lat, (*lists)[i].data(), (size_t)cnt * 4,
+                                       cudaMemcpyHostToDevice));
+                    list = dl.as<uint32_t>() + lat;
+                    lat += cnt;
+                }
+                ht.push_back(make_task(tp[i]->g, tp[i]->q, tp[i]->first, cnt, list, o));
+                owner.push_back(i);
+                maxw += (int)std::min<uint32_t>(cnt, 1u << 20);
+            }
+            big.assign(nt, {});
+            small.assign(nt, {});
+            if (ht.empty()) return;
+            const int nh = (int)ht.size();
+            dt.ensure(ctx, ht.size() * sizeof(WTask));
+            cd.ensure(ctx, (size_t)nh * 8 + 16);
+            IM_CUDA(cudaMemcpyAsync(dt.p, ht.data(), ht.size() * sizeof(WTask), cudaMemcpyHostToDevice, ctx->stream));
+            IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)nh * 8, ctx->stream));
+            EventTimer et(ctx);
+            launch_gs_rev(ctx, dt.as<WTask>(), nh, cd.as<uint32_t>(), cd.as<uint32_t>() + nh, wide,
+                          wide ? maxw : 0);
+            rev_ms += et.stop();
+            rev_launches += 1;
+            std::vector<unsigned char> hc((size_t)nt * CTL);
+            IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));
+            at = 0;
+            for (int i = 0; i < nt; ++i) {
+                uint32_t e = 0, nd = 0;
+                std::memcpy(&e, hc.data() + (size_t)i * CTL + 68, 4);
+                if (e) fail(IMIN_EDEVICE, "device invariant failed (reverse Global Sampling)");
+                std::memcpy(&nd, hc.data() + (size_t)i * CTL + 64, 4);
+                unsigned long long a8[8];
+                std::memcpy(a8, hc.data() + (size_t)i * CTL, 64);
+                for (int k = 0; k < 8; ++k) acc_rev[i][k] += a8[k];
+                if (nd) {
+                    std::vector<uint32_t> raw(nd);
+                    IM_CUDA(cudaMemcpy(raw.data(), defl.as<uint32_t>() + at, (size_t)nd * 4, cudaMemcpyDeviceToHost));
+                    for (uint32_t x : raw) ((x & 0x80000000u) ? big[i] : small[i]).push_back(x & 0x7fffffffu);
+                }
+                at += tp[i]->count;
+            }
+        };
+        std::vector<std::vector<uint32_t>> big1, small1, big2, small2;
+        rev_pass(false, nullptr, big1, small1);
+        size_t nbig1 = 0;
+        for (auto &v : big1) nbig1 += v.size();
+        if (nbig1) rev_pass(true, &big1, big2, small2);
+        else {
+            big2.assign(nt, {});
+            small2.assign(nt, {});
         }
-        dt.ensure(ctx, ht.size() * sizeof(WTask));
-        cd.ensure(ctx, (size_t)nt * 8 + 16);
-        IM_CUDA(cudaMemcpyAsync(dt.p, ht.data(), ht.size() * sizeof(WTask), cudaMemcpyHostToDevice, ctx->stream));
-        IM_CUDA(cudaMemsetAsync(cd.p, 0, (size_t)nt * 8, ctx->stream));
-        EventTimer et(ctx);
-        launch_gs_rev(ctx, dt.as<WTask>(), nt, cd.as<uint32_t>(), cd.as<uint32_t>() + nt);
-        rev_ms = et.stop();
-        rev_launches = 1;
-        std::vector<unsigned char> hc((size_t)nt * CTL);
-        IM_CUDA(cudaMemcpy(hc.data(), ctl.p, hc.size(), cudaMemcpyDeviceToHost));
-        uint32_t e = 0;
-        for (int i = 0; i < nt; ++i) {
-            uint32_t x;
-            std::memcpy(&x, hc.data() + (size_t)i * CTL + 68, 4);
-            e |= x;
-        }
-        if (e) fail(IMIN_EDEVICE, "device invariant failed (reverse Global Sampling)");
-        // the worlds left over, as lists of world offsets for the forward kernel
         std::vector<std::vector<uint32_t>> left(nt);
         size_t nleft = 0;
-        at = 0;
         for (int i = 0; i < nt; ++i) {
-            uint32_t nd = 0;
-            std::memcpy(&nd, hc.data() + (size_t)i * CTL + 64, 4);
-            std::memcpy(tp[i]->acc, hc.data() + (size_t)i * CTL, 64);
-            if (nd) {
-                left[i].resize(nd);
-                IM_CUDA(cudaMemcpy(left[i].data(), defl.as<uint32_t>() + at, (size_t)nd * 4, cudaMemcpyDeviceToHost));
-                for (uint32_t &x : left[i]) x &= 0x7fffffffu;
-                std::sort(left[i].begin(), left[i].end());
-                nleft += nd;
-            }
-            at += tp[i]->count;
+            for (auto *v : {&small1[i], &big2[i], &small2[i]}) left[i].insert(left[i].end(), v->begin(), v->end());
+            std::sort(left[i].begin(), left[i].end());
+            nleft += left[i].size();
         }
+        if (const char *trc = std::getenv("IMIN_TRACE"))
+            if (trc[0] == '1') {
+                size_t w = 0, s1 = 0, b2 = 0, s2 = 0;
+                for (int i = 0; i < nt; ++i) {
+                    w += tp[i]->count;
+                    s1 += small1[i].size();
+                    b2 += big2[i].size();
+                    s2 += small2[i].size();
+                }
+                std::fprintf(stderr,
+                             "[imin] reverse GS: %zu worlds; %zu too large for the narrow tables, %zu for the wide "
+                             "ones; %zu + %zu without store room; %.3f ms\n",
+                             w, nbig1, b2, s1, s2, rev_ms);
+            }
         std::vector<TaskRun *> keep;
         DBuf dleft;
         if (nleft) {
@@ -1381,8 +1434,6 @@ void sample_lrr(imin_ctx *ctx, std::vector<LrrJob> &jobs)
                 keep.push_back(tp[i]);
             }
         }
-        std::vector<std::array<unsigned long long, 8>> acc_rev(nt);
-        for (int i = 0; i < nt; ++i) std::memcpy(acc_rev[i].data(), tp[i]->acc, 64);
         if (!keep.empty()) {
             Runner run(ctx);
             run.run(keep, WF_UPPER | WF_STORE);

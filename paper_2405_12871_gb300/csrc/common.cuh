@@ -268,7 +268,8 @@ void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t
 
 // Global Sampling worlds traversed backwards from the target (gs_rev.cu): one warp per
 // world; worlds whose reverse set outgrows the warp's table are deferred (top bit).
-void launch_gs_rev(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t *d_claim, uint32_t *d_done);
+void launch_gs_rev(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t *d_claim, uint32_t *d_done, bool wide,
+                   int max_ctas);
 
 // LRR sequences (useq_cta.cu): the LRR set of every reached node of every world.
 struct UseqLaunch {

@@ -17,28 +17,42 @@
 // One warp per world.  X lives in a per-warp open-addressing table in shared memory
 // (node -> local id), with the live in-edges found between nodes of X and the nodes
 // entered directly from a seed.  A world whose X or edge list outgrows the table is
-// left to the forward kernel (deferred with the top bit), as is a world without store
-// room.  The coins are the forward edges' (edge id eid, Philox counter eid >> 2), so
+// deferred with the top bit (the host retries it with the wide tables, then with the
+// forward kernel), as is a world without store room (without the top bit).  The coins are the forward edges' (edge id eid, Philox counter eid >> 2), so
 // the sets are those of the forward kernel and of the oracle.
 #include "reach_cta.cuh"
 
 namespace gs_rev {
 
-constexpr int WARPS = 8;          // warps per CTA
-constexpr int XCAP = 128;         // nodes of X per world
-constexpr int HT = 256;           // hash slots (power of two, >= 2 XCAP)
-constexpr int ECAP = 256;         // live edges inside X per world
+// Two table sizes: the narrow one (8 warps per CTA, 3.7 KB per warp) takes every world;
+// the few worlds it cannot hold go to the wide one (one warp per CTA with 116 KB), and
+// only those that outgrow that to the forward kernel.
+template <int WARPS_, int XCAP_, int HT_, int HBITS_, int ECAP_>
+struct Cfg {
+    static constexpr int WARPS = WARPS_;   // warps per CTA
+    static constexpr int XCAP = XCAP_;     // nodes of X per world
+    static constexpr int HT = HT_;         // hash slots (power of two, >= 2 XCAP)
+    static constexpr int HBITS = HBITS_;   // log2(HT)
+    static constexpr int ECAP = ECAP_;     // live edges inside X per world
+};
+using Narrow = Cfg<8, 128, 256, 8, 256>;
+using Wide = Cfg<1, 4096, 8192, 13, 8192>;
 
+template <class C>
 struct WarpSmem {
-    int key[HT];
-    int val[HT];
-    int x[XCAP];                  // local id -> node
-    unsigned char flag[XCAP];     // bit 0: entered from a seed / reached; bit 1: newly reached
-    short eu[ECAP], ev[ECAP];     // live edge (local source, local target)
+    int key[C::HT];
+    int val[C::HT];
+    int x[C::XCAP];               // local id -> node
+    short eu[C::ECAP], ev[C::ECAP];   // live edge (local source, local target)
+    unsigned char flag[C::XCAP];  // bit 0: entered from a seed / reached from one
     int nx, ne, ovf;
 };
 
-__device__ __forceinline__ uint32_t hslot(int v) { return ((uint32_t)v * 2654435761u) >> 24; }   // 8 bits
+template <class C>
+__device__ __forceinline__ uint32_t hslot(int v)
+{
+    return ((uint32_t)v * 2654435761u) >> (32 - C::HBITS);
+}
 
 __device__ __forceinline__ bool bit_of(const uint32_t *bm, int v)
 {
@@ -46,14 +60,15 @@ __device__ __forceinline__ bool bit_of(const uint32_t *bm, int v)
 }
 
 // local id of node v in the table; -1 if absent
-__device__ __forceinline__ int lookup(WarpSmem &w, int v)
+template <class C>
+__device__ __forceinline__ int lookup(WarpSmem<C> &w, int v)
 {
-    uint32_t h = hslot(v);
-    for (int probe = 0; probe < HT; ++probe) {
+    uint32_t h = hslot<C>(v);
+    for (int probe = 0; probe < C::HT; ++probe) {
         const int k = w.key[h];
         if (k == v) return w.val[h];
         if (k < 0) return -1;
-        h = (h + 1) & (HT - 1);
+        h = (h + 1) & (C::HT - 1);
     }
     return -1;
 }
@@ -64,11 +79,13 @@ struct RArgs {
     uint32_t *claim, *done;
 };
 
-__global__ void __launch_bounds__(WARPS * 32) gs_rev_kernel(const RArgs a)
+template <class C>
+__global__ void __launch_bounds__(C::WARPS * 32, C::WARPS == 1 ? 1 : 4) gs_rev_kernel(const RArgs a)
 {
-    __shared__ WarpSmem sm[WARPS];
+    constexpr int WARPS = C::WARPS, XCAP = C::XCAP, HT = C::HT, ECAP = C::ECAP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem &w = sm[wid];
+    WarpSmem<C> &w = reinterpret_cast<WarpSmem<C> *>(smem_raw)[wid];
     for (int i = lane; i < HT; i += 32) w.key[i] = -1;
     __syncwarp();
     int ti = (int)((blockIdx.x * WARPS + wid) % (unsigned)a.ntasks);
@@ -116,7 +133,7 @@ __global__ void __launch_bounds__(WARPS * 32) gs_rev_kernel(const RArgs a)
         bool overflow = false;
         if (tn >= 0) {
             if (lane == 0) {
-                const uint32_t h = hslot(tn);
+                const uint32_t h = hslot<C>(tn);
                 w.key[h] = tn;
                 w.val[h] = 0;
                 w.x[0] = tn;
@@ -153,7 +170,7 @@ __global__ void __launch_bounds__(WARPS * 32) gs_rev_kernel(const RArgs a)
                     bool fresh = false;
                     int slot = -1;
                     if (inner) {
-                        uint32_t h = hslot(u);
+                        uint32_t h = hslot<C>(u);
                         for (int probe = 0; probe < HT; ++probe) {
                             const int old = atomicCAS(&w.key[h], -1, u);
                             if (old == -1) {
@@ -290,18 +307,35 @@ __global__ void __launch_bounds__(WARPS * 32) gs_rev_kernel(const RArgs a)
 
 }  // namespace gs_rev
 
-void launch_gs_rev(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t *d_claim, uint32_t *d_done)
+namespace {
+template <class C>
+void launch_cfg(imin_ctx *ctx, const gs_rev::RArgs &a, int max_ctas)
+{
+    const size_t smem = sizeof(gs_rev::WarpSmem<C>) * C::WARPS;
+    auto kern = gs_rev::gs_rev_kernel<C>;
+    IM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, C::WARPS * 32, smem) != cudaSuccess) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    int ctas = ctx->num_sms * std::max(nb, 1);
+    if (max_ctas > 0) ctas = std::min(ctas, max_ctas);
+    kern<<<std::max(ctas, 1), C::WARPS * 32, smem, ctx->stream>>>(a);
+    IM_CHECK_LAUNCH();
+}
+}  // namespace
+
+void launch_gs_rev(imin_ctx *ctx, const WTask *d_tasks, int ntasks, uint32_t *d_claim, uint32_t *d_done, bool wide,
+                   int max_ctas)
 {
     gs_rev::RArgs a;
     a.tasks = d_tasks;
     a.ntasks = ntasks;
     a.claim = d_claim;
     a.done = d_done;
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gs_rev::gs_rev_kernel, gs_rev::WARPS * 32, 0) != cudaSuccess) {
-        cudaGetLastError();
-        nb = 1;
-    }
-    gs_rev::gs_rev_kernel<<<ctx->num_sms * std::max(nb, 1), gs_rev::WARPS * 32, 0, ctx->stream>>>(a);
-    IM_CHECK_LAUNCH();
+    if (wide)
+        launch_cfg<gs_rev::Wide>(ctx, a, max_ctas);
+    else
+        launch_cfg<gs_rev::Narrow>(ctx, a, max_ctas);
 }
