@@ -651,6 +651,14 @@ double greedy_batch(imin_ctx *ctx, GreedyBufs &gb, std::vector<GreedyJob *> &job
         cudaEventDestroy(i0);
         cudaEventDestroy(i1);
     }
+    // candidates per argmax / histogram block (tuning hook IMIN_GREEDY_CAND_PER_BLOCK):
+    // every block of an instance adds its 2,048-bin histogram to the instance's with
+    // global atomics, so fewer, fuller blocks cost less per digit pass
+    long long per_blk = 512;
+    if (const char *env = std::getenv("IMIN_GREEDY_CAND_PER_BLOCK")) {
+        const long long v = std::strtoll(env, nullptr, 10);
+        if (v >= 256) per_blk = v;
+    }
     // per-instance state in one arena
     std::vector<GInst> gi(nj);
     std::vector<size_t> off(nj);
@@ -662,7 +670,7 @@ double greedy_batch(imin_ctx *ctx, GreedyBufs &gb, std::vector<GreedyJob *> &job
         const int32_t n = j.n, k = j.k;
         kmax = std::max(kmax, k);
         const int nblk = (int)std::min<long long>((long long)ctx->num_sms * 4,
-                                                   std::max<long long>(1, (ncand[i] + 2047) / 2048));
+                                                   std::max<long long>(1, (ncand[i] + per_blk - 1) / per_blk));
         // decrement grid: sized by the stored items (records or set elements)
         const long long items = j.c ? j.c->count : (long long)j.L->elems;
         const int unblk = (int)std::min<long long>((long long)ctx->num_sms * 8,
