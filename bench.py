@@ -260,13 +260,18 @@ def run_batch(args):
     G.solve(S, k, eps, delta, **kw)
     torch.cuda.synchronize()
     a = time.perf_counter()
-    plain = [G.solve(S, k, eps, delta, **kw) for (G, S, k, eps, delta, kw) in qs]
+    plain = [] if args.batch_only else [G.solve(S, k, eps, delta, **kw) for (G, S, k, eps, delta, kw) in qs]
     torch.cuda.synchronize()
     t_plain = time.perf_counter() - a
     a = time.perf_counter()
     batched = ctx.solve_batch(qs)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - a
+    if args.batch_only:
+        print(json.dumps({"mode": "batch-only", "instances": len(items), "batched_s": t_batch,
+                          "batched_kernel_launches": int(batched[0]["kernel_launches"]),
+                          "batched_stage_ms": [round(x, 1) for x in batched[0]["ms_stage"]]}), flush=True)
+        return 0
     diff = [i for i, (x, y) in enumerate(zip(plain, batched))
             if not (list(x["blockers"]) == list(y["blockers"]) and x["I_after"] == y["I_after"])]
     same = not diff
@@ -582,6 +587,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mc-check", action="store_true")
+    ap.add_argument("--batch-only", action="store_true", help="time the batched path alone (no plain replay)")
     ap.add_argument("--batch", type=int, default=0,
                     help="batched vs plain: the first N instances of the 512-instance Chung-Lu "
                          "batch recipe, solved one by one and as one imin_solve_batch")

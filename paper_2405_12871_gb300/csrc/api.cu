@@ -2003,27 +2003,42 @@ void solve_all(imin_ctx *ctx, std::vector<Inst *> &all)
     // Instances are admitted as a rolling window: at most `cap` in flight (each holds
     // its sample stores until it finishes), and a new one only while at least a quarter
     // of the device memory is free (the slot arenas count as free: they are caches).
-    int cap = 64;
+    // The window starts at 64 and widens by 64 after every step that ends with more
+    // than half of the device memory free, up to 512: instances grow their stores over
+    // several steps, so the window only widens once the ones in flight have shown what
+    // they hold.  IMIN_BATCH_ACTIVE="c" fixes the window at c; "c:m" starts it at c and
+    // widens it by c up to m.
+    int cap = 64, cap_max = 512;
     if (const char *env = std::getenv("IMIN_BATCH_ACTIVE")) {
-        const long v = std::strtol(env, nullptr, 10);
-        if (v >= 1) cap = (int)v;
+        char *end = nullptr;
+        const long v = std::strtol(env, &end, 10);
+        if (v >= 1) {
+            cap = cap_max = (int)v;
+            if (end && *end == ':') {
+                const long m = std::strtol(end + 1, nullptr, 10);
+                if (m >= v) cap_max = (int)m;
+            }
+        }
     }
+    const int cap_step = cap;
+    auto free_frac = [&]() {
+        size_t freeb = 0, totalb = 0;
+        cudaMemGetInfo(&freeb, &totalb);
+        cudaGetLastError();
+        freeb += ctx->slots.bytes + ctx->slots_lower.bytes + ctx->big_slots.bytes + ctx->slots_final.bytes;
+        return totalb ? (double)freeb / (double)totalb : 0.0;
+    };
     size_t next = 0;
     auto admit = [&]() {
         while (next < all.size() && (int)sch.active.size() < cap) {
-            if (!sch.active.empty()) {
-                size_t freeb = 0, totalb = 0;
-                cudaMemGetInfo(&freeb, &totalb);
-                cudaGetLastError();
-                freeb += ctx->slots.bytes + ctx->slots_lower.bytes + ctx->big_slots.bytes + ctx->slots_final.bytes;
-                if (freeb < totalb / 4) break;
-            }
+            if (!sch.active.empty() && free_frac() < 0.25) break;
             sch.add(all[next++]);
         }
     };
     admit();
     while (!sch.active.empty()) {
         sch.step();
+        if (cap < cap_max && next < all.size() && free_frac() > 0.5) cap = std::min(cap_max, cap + cap_step);
         admit();
     }
     sch.ms[7] = total.ms();

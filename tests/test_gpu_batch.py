@@ -54,10 +54,11 @@ def test_mixed_batch_equals_alone_and_oracle(ctx):
         G.free()
 
 
-@pytest.mark.parametrize("window", [None, "3"])
+@pytest.mark.parametrize("window", [None, "3", "2:6"])
 def test_batch_of_many_small_instances(ctx, monkeypatch, window):
-    """All ten instances in flight at once, or a rolling window of three admitted as
-    others finish: the results equal the one-at-a-time solves either way."""
+    """All ten instances in flight at once, a rolling window of three admitted as
+    others finish, or a window that starts at two and widens by two per step up to six:
+    the results equal the one-at-a-time solves every way."""
     if window:
         monkeypatch.setenv("IMIN_BATCH_ACTIVE", window)
     gs = [synth.chung_lu(int(n), 10.0, 2.1, seed=20 + i)
