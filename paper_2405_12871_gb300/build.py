@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libimin.so")
 SOURCES = ["sampler.cu", "sampler_cta.cu", "reach_cta_256.cu", "reach_cta_512.cu", "reach_cta_1024.cu",
-           "greedy.cu", "graph.cu", "vs.cu", "api.cu", "noalloc.cu", "final_cta.cu", "useq_cta.cu", "gs_rev.cu"]
+           "greedy.cu", "graph.cu", "vs.cu", "api.cu", "noalloc.cu", "final_cta.cu", "useq_cta.cu", "gs_rev.cu",
+           "hot_view.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

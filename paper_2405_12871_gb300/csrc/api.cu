@@ -175,6 +175,9 @@ struct TaskRun {
     std::function<void(uint32_t)> grow;   // enlarge the task's store for nd worlds; updates out
     unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t claimed_main = 0;
+    // relabelled forward index of the query (reach-only worlds without blocked nodes on
+    // CTA slots only; the warp-per-world kernel reads the original index)
+    const HotView *hv = nullptr;
 };
 
 constexpr size_t CTL = 128;   // per-task control block: acc[8] | n_deferred | err
@@ -433,9 +436,21 @@ struct Runner {
         SlotCfg cfg = cfg_for(flags, nmax, mmax, nSmax, false);
         DBuf &arena = cfg.lower ? ctx->slots_lower : ctx->slots;
         size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
+        // a task on the relabelled index reads its ranges, groups and seeds from the view
+        auto with_view = [&](WTask w, const TaskRun *tr, bool cta) {
+            const HotView *h = tr->hv;
+            if (cta && h && h->on && tr->q.nB == 0 && !(flags & (WF_REACH | WF_LOWER | WF_UPPER))) {
+                w.rng = h->rng.as<int2>();
+                w.gid = h->gid.as<uint32_t>();
+                w.ce = h->ce.as<uint4>();
+                w.q.S = h->S.as<int32_t>();
+            }
+            return w;
+        };
         std::vector<WTask> ht;
         for (int i = 0; i < n; ++i)
-            ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, T[i]->list, T[i]->out));
+            ht.push_back(with_view(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, T[i]->list, T[i]->out),
+                                   T[i], cfg.ctas > 0));
         launch(ht, T[0]->g, flags, cfg, arena, layout);
         std::vector<unsigned char> hc((size_t)n * CTL);
         std::vector<uint32_t> claims(n);
@@ -478,8 +493,9 @@ struct Runner {
                     if (L[i].empty()) continue;
                     IM_CUDA(cudaMemcpy(lists.as<uint32_t>() + at, L[i].data(), L[i].size() * 4,
                                        cudaMemcpyHostToDevice));
-                    lt.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, (uint32_t)L[i].size(),
-                                           lists.as<uint32_t>() + at, T[i]->out));
+                    lt.push_back(with_view(make_task(T[i]->g, T[i]->q, T[i]->first, (uint32_t)L[i].size(),
+                                                     lists.as<uint32_t>() + at, T[i]->out),
+                                           T[i], pass == 0 && cfg.ctas > 0));
                     at += L[i].size();
                 }
                 // a deferred world was claimed before the early exit, so it must complete:
@@ -658,6 +674,7 @@ struct StopSpec {
     uint64_t key;
     uint32_t tag, inst;
     SpreadEst est;
+    const HotView *hv = nullptr;   // relabelled forward index of the query, if built
 };
 
 void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
@@ -716,6 +733,7 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
             t.count = (uint32_t)cnt;
             t.out.world_spread = ctx->stop_spread.as<uint32_t>() + soff[i];
             t.out.stop_T = T[i] - sum[i];
+            t.hv = specs[i].hv;
             tp.push_back(&t);
             idx.push_back(i);
         }
@@ -785,6 +803,76 @@ SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double b
 }
 
 // ---------------------------------------------------------------------------
+// Relabelled forward index of a query (hot_view.cu) for its reach-only stopping rules.
+// It changes no result (the rules count nodes, and every edge keeps its coin); it pays
+// where the worlds' visited structures live in global memory.  IMIN_HOT_VIEW=0 turns it
+// off, =2 builds it on every graph (test hook); IMIN_HOT_WORLDS sets the worlds of the
+// reach counts that order the labels (default 2,048, of a stream tag no estimate draws).
+// ---------------------------------------------------------------------------
+constexpr uint32_t TAG_HOT = 0xFFFFFFF1u;
+
+struct HotStats {
+    double kernel_ms = 0.0;
+    uint64_t launches = 0;
+};
+
+HotStats maybe_hot_view(imin_ctx *ctx, const imin_graph *g, const Query &q, uint64_t key, uint32_t inst,
+                        HotView &hv)
+{
+    HotStats hs;
+    hv.release();
+    const char *env = std::getenv("IMIN_HOT_VIEW");
+    const bool force = env && env[0] == '2';
+    if (env && env[0] == '0') return hs;
+    if (!force && !(g->tuned_ctas > 0 && !g->tuned_smem && g->n >= (1 << 18))) return hs;
+    if (!q.blocked.empty()) return hs;
+    uint32_t W0 = 2048;
+    if (const char *we = std::getenv("IMIN_HOT_WORLDS")) {
+        const long v = std::strtol(we, nullptr, 10);
+        if (v >= 1 && v <= 6000) W0 = (uint32_t)v;
+    }
+    DBuf counts;
+    counts.ensure(ctx, (size_t)g->n * 8);
+    IM_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)g->n * 8, ctx->stream));
+    TaskRun t;
+    t.g = g;
+    t.q = qdev(q, key, TAG_HOT, inst);
+    t.first = 0;
+    t.count = W0;
+    t.out.reach = counts.as<unsigned long long>();
+    std::vector<TaskRun *> tp{&t};
+    Runner run(ctx);
+    run.run(tp, WF_REACH);
+    hs.kernel_ms = run.kernel_ms;
+    hs.launches = (uint64_t)run.launches;
+    hs.launches += (uint64_t)hot_view_build(ctx, g, counts.as<unsigned long long>(), W0, q.dS.as<int32_t>(),
+                                            (int32_t)q.S.size(), hv);
+    return hs;
+}
+
+// the candidates' blocked lists in the view's labels
+int hot_view_blocked(imin_ctx *ctx, HotView &hv, const Query *const qb[3], const bool use[3])
+{
+    if (!hv.on) return 0;
+    int launches = 0;
+    int64_t tot = 0;
+    for (int c = 0; c < 3; ++c) {
+        hv.boff[c] = tot;
+        if (use[c]) tot += (int64_t)qb[c]->blocked.size();
+    }
+    hv.B.ensure(ctx, (size_t)std::max<int64_t>(tot, 1) * 4);
+    for (int c = 0; c < 3; ++c)
+        if (use[c] && !qb[c]->blocked.empty())
+        {
+            hot_view_map(ctx, hv, qb[c]->dB.as<int32_t>(), (int32_t)qb[c]->blocked.size(),
+                         hv.B.as<int32_t>() + hv.boff[c]);
+            ++launches;
+        }
+    IM_CUDA(cudaStreamSynchronize(ctx->stream));
+    return launches;
+}
+
+// ---------------------------------------------------------------------------
 // Final estimates (Algorithm 1, line 4): the (gamma, delta)-estimates of the residual
 // spread of up to three candidate blocker sets, all on the worlds of stream tag 5.
 // One traversal per world serves every candidate (final_cta.cu); each candidate
@@ -802,6 +890,7 @@ struct FinalSpec {
     uint32_t inst;
     double spread_hint;   // expected spread without blockers (sizes the fused queue; 0 = unknown)
     SpreadEst est[3];
+    const HotView *hv;    // relabelled forward index with the candidates' blocked lists (or null)
 };
 
 struct FinalStats {
@@ -958,8 +1047,16 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
             t.S = f.q->dS.as<int32_t>();
             t.nS = (int32_t)f.q->S.size();
             t.cands = cands;
+            const bool view = f.hv && f.hv->on;
+            if (view) {
+                t.rng = f.hv->rng.as<int2>();
+                t.gid = f.hv->gid.as<uint32_t>();
+                t.ce = f.hv->ce.as<uint4>();
+                t.S = f.hv->S.as<int32_t>();
+            }
             for (int c = 0; c < 3; ++c) {
-                t.B[c] = f.use[c] ? f.qb[c]->dB.as<int32_t>() : nullptr;
+                t.B[c] = f.use[c] ? (view ? f.hv->B.as<int32_t>() + f.hv->boff[c] : f.qb[c]->dB.as<int32_t>())
+                                  : nullptr;
                 t.nB[c] = f.use[c] ? (int32_t)f.qb[c]->blocked.size() : 0;
                 t.stop_T[c] = ((cands >> c) & 1u) ? T[i][c] - sum[i][c] : 0ull;
             }
@@ -1553,6 +1650,7 @@ struct Inst {
     DBuf credC1, credL1, inB;
     int stage = 0;            // Stage of the scheduler
     Query qb[3];              // final-estimate queries (S with B_L / B_U / B_R blocked)
+    HotView hv;               // relabelled forward index for the spread and final estimates
 };
 
 void put(int32_t *dst, const std::vector<int32_t> &src)
@@ -1751,6 +1849,8 @@ struct Scheduler {
             prepare_query(ctx, I.g, I.qb[c], I.q.S.data(), (int32_t)I.q.S.size(), cand[c]->data(),
                           (int32_t)cand[c]->size(), true);
         }
+        const Query *qb[3] = {&I.qb[0], &I.qb[1], &I.qb[2]};
+        reach_launches += (uint64_t)hot_view_blocked(ctx, I.hv, qb, use);
         I.stage = ST_FINAL;
     }
 
@@ -1771,6 +1871,7 @@ struct Scheduler {
             res->ratio_lb = gr * one_m_inv_e_m_eps * (I.I_hat - res->I_after[1]) / res->DU_hat;
         }
         for (int c = 0; c < 3; ++c) I.qb[c].release();
+        I.hv.release();
         I.stage = ST_DONE;
         I.done = true;
     }
@@ -1825,7 +1926,11 @@ struct Scheduler {
         std::vector<Inst *> fin;
         for (Inst *I : active) {
             if (I->stage == ST_IHAT) {
-                sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
+                autotune_reach(ctx, I->g, I->q);
+                const HotStats hs = maybe_hot_view(ctx, I->g, I->q, I->key, I->inst, I->hv);
+                kms[0] += hs.kernel_ms;
+                reach_launches += hs.launches;
+                sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}, &I->hv});
                 ihat.push_back(I);
             } else if (I->stage == ST_FINAL) {
                 FinalSpec f{};
@@ -1840,6 +1945,7 @@ struct Scheduler {
                 f.key = I->key;
                 f.inst = I->inst;
                 f.spread_hint = I->I_hat;
+                f.hv = &I->hv;
                 fsp.push_back(f);
                 fin.push_back(I);
             }
@@ -2327,6 +2433,11 @@ int imin_final_estimates(imin_graph *g, const int32_t *S, int32_t nS, int32_t n_
         f.key = key;
         f.inst = inst;
         f.spread_hint = spread_hint > 0.0 ? spread_hint : 0.0;
+        autotune_reach(ctx, g, q);
+        HotView hv;
+        maybe_hot_view(ctx, g, q, key, inst, hv);
+        hot_view_blocked(ctx, hv, f.qb, f.use);
+        f.hv = &hv;
         std::vector<FinalSpec> v{f};
         final_estimates(ctx, v);
         for (int c = 0; c < n_cand; ++c) {

@@ -227,6 +227,8 @@ int world_kernel_blocks_per_sm(uint32_t flags, int U);
 struct WTask {
     const int32_t *row_ptr;
     const uint4 *ce;
+    const int2 *rng;       // relabelled forward index (hot_view.cu), else null: label -> [b, e)
+    const uint32_t *gid;   // relabelled forward index: group -> its original index (the coin counter)
     const int32_t *in_ptr, *in_src, *in_eid;
     const uint32_t *in_thr;
     int32_t n;
@@ -245,6 +247,8 @@ WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t
 struct FTask {
     const int32_t *row_ptr;
     const uint4 *ce;
+    const int2 *rng;                 // relabelled forward index, as in WTask (else null)
+    const uint32_t *gid;
     const int32_t *S;                // device, nS seeds
     int32_t nS;
     uint32_t cands;                  // candidates served (bits 0..2)
@@ -321,8 +325,42 @@ void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_gr
 int32_t device_reach_set(imin_ctx *ctx, const imin_graph *g, const int32_t *dS, int32_t nS,
                          const uint32_t *seed_bm, const uint32_t *blk_bm, DBuf &out);
 
+// Relabelled forward index of one query (hot_view.cu).  The reach-only stopping rules
+// (spread estimates, Algorithm 4 line 4; final estimates, Algorithm 1 line 4) count the
+// nodes each world reaches, and a count does not depend on the nodes' labels as long as
+// every edge keeps its coin.  Nodes are relabelled by how often a short run of the
+// query's worlds reaches them (most often first); each node's out-edges are copied with
+// their whole 4-edge groups into a new group array in label order, each new group
+// keeping its original index, from which its coins are drawn.  The worlds' visited
+// bitmaps and candidate maps then touch fewer 32-byte sectors, and the group records of
+// the nodes most often reached lie together.
+struct HotView {
+    bool on = false;
+    int32_t n = 0;
+    DBuf perm;   // int32[n]: node -> label
+    DBuf rng;    // int2[n]: label -> [b, e) in the new edge positions
+    DBuf ce;     // group records in label order: targets relabelled, thresholds kept
+    DBuf gid;    // uint32 per new group: its original group index
+    DBuf S;      // the seeds' labels
+    DBuf B;      // blocked nodes' labels (the final candidates' lists, concatenated)
+    int64_t boff[3] = {0, 0, 0};
+    void release()
+    {
+        for (DBuf *b : {&perm, &rng, &ce, &gid, &S, &B}) b->release();
+        on = false;
+    }
+};
+// Builds `hv` from per-node reach counts (each <= max_count) of the query's worlds on
+// g; S: device, nS seeds.  Leaves hv.on false when the relabelled edge positions would
+// not fit in int32.  Returns the kernel launches it made.
+int hot_view_build(imin_ctx *ctx, const imin_graph *g, const unsigned long long *d_counts, uint32_t max_count,
+                    const int32_t *d_S, int32_t nS, HotView &hv);
+// dst[i] = label of src[i] (device arrays, cnt entries)
+void hot_view_map(imin_ctx *ctx, const HotView &hv, const int32_t *d_src, int32_t cnt, int32_t *d_dst);
+
 // exclusive scan of n int64 values in place (d_tmp: >= scan_tmp_bytes(n) bytes)
 size_t scan_tmp_bytes(int64_t n);
+int scan_launches(int64_t n);   // kernel launches of one scan of n values
 void exclusive_scan_i64(imin_ctx *ctx, long long *d, int64_t n, void *d_tmp);
 void exclusive_scan_i32(imin_ctx *ctx, int32_t *d, int64_t n, void *d_tmp);
 void fill_bitmap(imin_ctx *ctx, uint32_t *bm, size_t words, const int32_t *d_nodes, int32_t cnt);

@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
         }
         __syncthreads();
         unsigned long long wedges = 0;
-        const Fwd fwd{T.row_ptr, T.ce, reach_cta::graph_l2_policy(a.l2_keep != 0)};
+        const Fwd fwd{T.row_ptr, T.ce, reach_cta::graph_l2_policy(a.l2_keep != 0), T.rng, T.gid};
         const int tail = bfs_multi<BD>(fwd, K, nib, Q, nS, sh, wedges, a.qcap, &s_ovf);
         if (tail < 0) {
             // overflow: wipe the map (dropped entries left bits that the queue cannot

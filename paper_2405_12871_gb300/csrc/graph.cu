@@ -170,6 +170,13 @@ void excl_scan(imin_ctx *ctx, T *d, int64_t n, void *tmp)
 
 }  // namespace
 
+int scan_launches(int64_t n)
+{
+    if (n <= 0) return 0;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return tiles > 1 ? 2 + scan_launches(tiles) : 1;
+}
+
 size_t scan_tmp_bytes(int64_t n)
 {
     size_t total = 0;

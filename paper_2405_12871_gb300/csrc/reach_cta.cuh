@@ -161,11 +161,19 @@ struct Fwd {
     static constexpr bool kCountEdges = true;   // the scanned edges are reported
     const int32_t *row_ptr;
     const uint4 *ce;
-    uint64_t pol;   // L2 policy of the group loads
+    uint64_t pol;                    // L2 policy of the group loads
+    const int2 *rng = nullptr;       // relabelled index (HotView): label -> [b, e)
+    const uint32_t *gid = nullptr;   // relabelled index: group -> original group index
     __device__ __forceinline__ void range(int u, int &b, int &e) const
     {
-        b = row_ptr[u];
-        e = row_ptr[u + 1];
+        if (rng) {
+            const int2 r = __ldg(rng + u);
+            b = r.x;
+            e = r.y;
+        } else {
+            b = row_ptr[u];
+            e = row_ptr[u + 1];
+        }
     }
     __device__ __forceinline__ static int first(int b) { return b >> 2; }
     __device__ __forceinline__ static int count(int b, int e) { return e > b ? ((e + 3) >> 2) - (b >> 2) : 0; }
@@ -176,7 +184,8 @@ struct Fwd {
         const uint4 cu = ld_group_half(p, pol);
         c4 = make_int4((int)cu.x, (int)cu.y, (int)cu.z, (int)cu.w);
         const uint4 t4 = ld_group_half(p + 1, pol);
-        const uint4 w = philox10_w(make_uint4((uint32_t)g, K.j, K.tag, K.inst), K.klo, K.khi);
+        const uint32_t gc = gid ? __ldg(gid + g) : (uint32_t)g;   // the coin counter
+        const uint4 w = philox10_w(make_uint4(gc, K.j, K.tag, K.inst), K.klo, K.khi);
         uint32_t m = (uint32_t)((w.x >> 8) < t4.x) | ((uint32_t)((w.y >> 8) < t4.y) << 1) |
                      ((uint32_t)((w.z >> 8) < t4.z) << 2) | ((uint32_t)((w.w >> 8) < t4.w) << 3);
         // edges of the group outside [ob, oe) belong to neighbouring nodes
@@ -553,7 +562,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
         }
         __syncthreads();
         unsigned long long wedges = 0;
-        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0)};
+        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0), T.rng, T.gid};
         const int tail = bfs<BD, false>(fwd, NoRec{}, K, bm, Q, nS, sh, wedges);
 
         // ---- upper bound: target from V'_s, reverse BFS inside the reached set ----
