@@ -175,9 +175,6 @@ struct TaskRun {
     std::function<void(uint32_t)> grow;   // enlarge the task's store for nd worlds; updates out
     unsigned long long acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     uint32_t claimed_main = 0;
-    // relabelled forward index of the query (reach-only worlds without blocked nodes on
-    // CTA slots only; the warp-per-world kernel reads the original index)
-    const HotView *hv = nullptr;
 };
 
 constexpr size_t CTL = 128;   // per-task control block: acc[8] | n_deferred | err
@@ -436,21 +433,9 @@ struct Runner {
         SlotCfg cfg = cfg_for(flags, nmax, mmax, nSmax, false);
         DBuf &arena = cfg.lower ? ctx->slots_lower : ctx->slots;
         size_t &layout = cfg.lower ? ctx->slots_lower_layout : ctx->slots_layout;
-        // a task on the relabelled index reads its ranges, groups and seeds from the view
-        auto with_view = [&](WTask w, const TaskRun *tr, bool cta) {
-            const HotView *h = tr->hv;
-            if (cta && h && h->on && tr->q.nB == 0 && !(flags & (WF_REACH | WF_LOWER | WF_UPPER))) {
-                w.rng = h->rng.as<int2>();
-                w.gid = h->gid.as<uint32_t>();
-                w.ce = h->ce.as<uint4>();
-                w.q.S = h->S.as<int32_t>();
-            }
-            return w;
-        };
         std::vector<WTask> ht;
         for (int i = 0; i < n; ++i)
-            ht.push_back(with_view(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, T[i]->list, T[i]->out),
-                                   T[i], cfg.ctas > 0));
+            ht.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, T[i]->count, T[i]->list, T[i]->out));
         launch(ht, T[0]->g, flags, cfg, arena, layout);
         std::vector<unsigned char> hc((size_t)n * CTL);
         std::vector<uint32_t> claims(n);
@@ -493,9 +478,8 @@ struct Runner {
                     if (L[i].empty()) continue;
                     IM_CUDA(cudaMemcpy(lists.as<uint32_t>() + at, L[i].data(), L[i].size() * 4,
                                        cudaMemcpyHostToDevice));
-                    lt.push_back(with_view(make_task(T[i]->g, T[i]->q, T[i]->first, (uint32_t)L[i].size(),
-                                                     lists.as<uint32_t>() + at, T[i]->out),
-                                           T[i], pass == 0 && cfg.ctas > 0));
+                    lt.push_back(make_task(T[i]->g, T[i]->q, T[i]->first, (uint32_t)L[i].size(),
+                                           lists.as<uint32_t>() + at, T[i]->out));
                     at += L[i].size();
                 }
                 // a deferred world was claimed before the early exit, so it must complete:
@@ -674,7 +658,6 @@ struct StopSpec {
     uint64_t key;
     uint32_t tag, inst;
     SpreadEst est;
-    const HotView *hv = nullptr;   // relabelled forward index of the query, if built
 };
 
 void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
@@ -733,7 +716,6 @@ void stop_rules(imin_ctx *ctx, std::vector<StopSpec> &specs)
             t.count = (uint32_t)cnt;
             t.out.world_spread = ctx->stop_spread.as<uint32_t>() + soff[i];
             t.out.stop_T = T[i] - sum[i];
-            t.hv = specs[i].hv;
             tp.push_back(&t);
             idx.push_back(i);
         }
@@ -803,9 +785,11 @@ SpreadEst stop_rule(imin_ctx *ctx, const imin_graph *g, const Query &q, double b
 }
 
 // ---------------------------------------------------------------------------
-// Relabelled forward index of a query (hot_view.cu) for its reach-only stopping rules.
-// It changes no result (the rules count nodes, and every edge keeps its coin); it pays
-// where the worlds' visited structures live in global memory.  IMIN_HOT_VIEW=0 turns it
+// Relabelled forward index of a query (hot_view.cu) for its fused final estimates.
+// It changes no result (the estimates count nodes, and every edge keeps its coin); it
+// pays where the worlds' candidate maps live in global memory and miss L2 (on the 1M-node
+// Chung-Lu workload the final estimates take 14% less time; the spread estimate's 1-bit
+// visited bitmaps gained nothing measurable and keep the original index).  IMIN_HOT_VIEW=0 turns it
 // off, =2 builds it on every graph (test hook); IMIN_HOT_WORLDS sets the worlds of the
 // reach counts that order the labels (default 2,048, of a stream tag no estimate draws).
 // ---------------------------------------------------------------------------
@@ -1650,7 +1634,8 @@ struct Inst {
     DBuf credC1, credL1, inB;
     int stage = 0;            // Stage of the scheduler
     Query qb[3];              // final-estimate queries (S with B_L / B_U / B_R blocked)
-    HotView hv;               // relabelled forward index for the spread and final estimates
+    HotView hv;               // relabelled forward index for the final estimates
+    bool hv_built = false;
 };
 
 void put(int32_t *dst, const std::vector<int32_t> &src)
@@ -1849,8 +1834,6 @@ struct Scheduler {
             prepare_query(ctx, I.g, I.qb[c], I.q.S.data(), (int32_t)I.q.S.size(), cand[c]->data(),
                           (int32_t)cand[c]->size(), true);
         }
-        const Query *qb[3] = {&I.qb[0], &I.qb[1], &I.qb[2]};
-        reach_launches += (uint64_t)hot_view_blocked(ctx, I.hv, qb, use);
         I.stage = ST_FINAL;
     }
 
@@ -1926,13 +1909,19 @@ struct Scheduler {
         std::vector<Inst *> fin;
         for (Inst *I : active) {
             if (I->stage == ST_IHAT) {
-                autotune_reach(ctx, I->g, I->q);
-                const HotStats hs = maybe_hot_view(ctx, I->g, I->q, I->key, I->inst, I->hv);
-                kms[0] += hs.kernel_ms;
-                reach_launches += hs.launches;
-                sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}, &I->hv});
+                sp.push_back(StopSpec{I->g, &I->q, I->beta, I->delta / 6.0, I->key, 0u, I->inst, SpreadEst{}});
                 ihat.push_back(I);
             } else if (I->stage == ST_FINAL) {
+                if (!I->hv_built) {
+                    // the relabelled index, built once before the instance's final estimates
+                    autotune_reach(ctx, I->g, I->q);
+                    const HotStats hs = maybe_hot_view(ctx, I->g, I->q, I->key, I->inst, I->hv);
+                    const Query *qb[3] = {&I->qb[0], &I->qb[1], &I->qb[2]};
+                    const bool use[3] = {I->do_L, I->do_U, I->do_R};
+                    kms[0] += hs.kernel_ms;
+                    reach_launches += hs.launches + (uint64_t)hot_view_blocked(ctx, I->hv, qb, use);
+                    I->hv_built = true;
+                }
                 FinalSpec f{};
                 f.g = I->g;
                 f.q = &I->q;

@@ -227,8 +227,6 @@ int world_kernel_blocks_per_sm(uint32_t flags, int U);
 struct WTask {
     const int32_t *row_ptr;
     const uint4 *ce;
-    const int2 *rng;       // relabelled forward index (hot_view.cu), else null: label -> [b, e)
-    const uint32_t *gid;   // relabelled forward index: group -> its original index (the coin counter)
     const int32_t *in_ptr, *in_src, *in_eid;
     const uint32_t *in_thr;
     int32_t n;
@@ -247,8 +245,8 @@ WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t
 struct FTask {
     const int32_t *row_ptr;
     const uint4 *ce;
-    const int2 *rng;                 // relabelled forward index, as in WTask (else null)
-    const uint32_t *gid;
+    const int2 *rng;                 // relabelled forward index (HotView), else null: label -> [b, e)
+    const uint32_t *gid;             // relabelled forward index: group -> original group index
     const int32_t *S;                // device, nS seeds
     int32_t nS;
     uint32_t cands;                  // candidates served (bits 0..2)
@@ -325,9 +323,8 @@ void launch_tasks(imin_ctx *ctx, const WTask *d_tasks, int ntasks, const imin_gr
 int32_t device_reach_set(imin_ctx *ctx, const imin_graph *g, const int32_t *dS, int32_t nS,
                          const uint32_t *seed_bm, const uint32_t *blk_bm, DBuf &out);
 
-// Relabelled forward index of one query (hot_view.cu).  The reach-only stopping rules
-// (spread estimates, Algorithm 4 line 4; final estimates, Algorithm 1 line 4) count the
-// nodes each world reaches, and a count does not depend on the nodes' labels as long as
+// Relabelled forward index of one query (hot_view.cu).  The final estimates (Algorithm
+// 1, line 4) count the nodes each world reaches, and a count does not depend on the nodes' labels as long as
 // every edge keeps its coin.  Nodes are relabelled by how often a short run of the
 // query's worlds reaches them (most often first); each node's out-edges are copied with
 // their whole 4-edge groups into a new group array in label order, each new group

@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_world_kernel(const CArgs a)
         }
         __syncthreads();
         unsigned long long wedges = 0;
-        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0), T.rng, T.gid};
+        const Fwd fwd{T.row_ptr, T.ce, graph_l2_policy(a.l2_keep != 0)};
         const int tail = bfs<BD, false>(fwd, NoRec{}, K, bm, Q, nS, sh, wedges);
 
         // ---- upper bound: target from V'_s, reverse BFS inside the reached set ----

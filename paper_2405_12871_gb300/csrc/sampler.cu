@@ -601,8 +601,6 @@ WTask make_task(const imin_graph *g, const QueryDev &q, uint64_t first, uint32_t
     WTask t;
     t.row_ptr = g->row_ptr.as<int32_t>();
     t.ce = g->ce.as<uint4>();
-    t.rng = nullptr;
-    t.gid = nullptr;
     t.in_ptr = g->in_ptr.as<int32_t>();
     t.in_src = g->in_src.as<int32_t>();
     t.in_eid = g->in_eid.as<int32_t>();

@@ -4,7 +4,8 @@ CTAs per SM, visited bitmaps in global memory), compared with the oracle element
 element -- every node's reach count and every world's spread.  The oracle's world
 loop is split over the host cores (``oracle_pool``).  Also: the three final
 estimates of a full-size solve, fused and one candidate at a time, agree exactly, and
-the whole solve is the same on the relabelled forward index and on the original one.
+the whole solve is the same with the final estimates on the relabelled forward index
+and on the original one.
 """
 import numpy as np
 import pytest
@@ -56,8 +57,8 @@ def test_cl1m_solve_final_estimates_fused_equal_separate(cl1m, monkeypatch):
     assert list(fused["blockers"]) == list(sep["blockers"])
     assert fused["n_final"] == sep["n_final"] and fused["I_after"] == sep["I_after"]
     assert fused["n_spread"] == sep["n_spread"] and fused["I_hat"] == sep["I_hat"]
-    # the spread and final estimates above ran on the relabelled forward index (on by
-    # default for this graph); on the original labels every result is the same
+    # the fused final estimates above ran on the relabelled forward index (on by default
+    # for this graph); on the original labels every result is the same
     monkeypatch.delenv("IMIN_FINAL_FUSED")
     monkeypatch.setenv("IMIN_HOT_VIEW", "0")
     plain = G.solve(S, **kw)

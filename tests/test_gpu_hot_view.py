@@ -1,7 +1,7 @@
-"""GPU parity of the relabelled forward index (HotView) that the spread and final
-estimates traverse: nodes relabelled by reach frequency, edges copied with their whole
-4-edge groups, coins drawn from each group's original index.  The stopping rules count
-nodes, so every result must equal the one on the original labels and the oracle's."""
+"""GPU parity of the relabelled forward index (HotView) that the fused final estimates
+traverse: nodes relabelled by reach frequency, edges copied with their whole 4-edge
+groups, coins drawn from each group's original index.  The estimates count nodes, so
+every result must equal the one on the original labels and the oracle's."""
 import numpy as np
 import pytest
 
@@ -24,10 +24,10 @@ def ctx():
                                    {"IMIN_HOT_WORLDS": "1"}, {"IMIN_HOT_WORLDS": "6000"},
                                    {"IMIN_REACH_SMEM": "0", "IMIN_AUTOTUNE": "0"}])
 def test_solve_on_view_equals_oracle(ctx, monkeypatch, hooks):
-    """Spread and final estimates on the view (forced on a 20K-node Chung-Lu graph):
-    in several chunks, with queue overflows re-run one candidate at a time on the
-    original labels, with degenerate (1 world: two count values) and many (6,000)
-    count values, and on global visited bitmaps; then the same solve without it."""
+    """Final estimates on the view (forced on a 20K-node Chung-Lu graph): in several
+    chunks, with queue overflows re-run one candidate at a time on the original labels,
+    with degenerate (1 world: two count values) and many (6,000) count values, and
+    without the autotuner; then the same solve without the view."""
     for k, v in hooks.items():
         monkeypatch.setenv(k, v)
     g = synth.chung_lu(20_000, 10.0, 2.1, seed=7)
