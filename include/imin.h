@@ -166,8 +166,13 @@ int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *bloc
  * (gamma, delta)-estimate of E[I_{G[V \ B[c]}](s)] by the stopping rule (the reading
  * imin_solve uses), all on the worlds of stream tag 5 of (key, inst): the same values
  * imin_solve reports in I_after / n_final for its candidates.  One traversal per world
- * serves every candidate.  spread_hint: the expected spread without blockers if known
- * (sizes the traversal queue; 0 = unknown).  Outputs: I_after[n_cand], n_worlds[n_cand]
+ * serves every candidate.  On graphs of at least 2^18 nodes whose worlds keep their
+ * visited structures in global memory, the traversal runs on a relabelled copy of the
+ * forward index (nodes ordered by how often 2,048 worlds of a stream tag no estimate
+ * draws reach them; each edge keeps its coin), which changes no value and takes about
+ * 16 B per node + 40 B per edge of device memory while the call runs (imin_solve holds
+ * it from its final estimates to its return).  spread_hint: the expected spread without
+ * blockers if known (sizes the traversal queue; 0 = unknown).  Outputs: I_after[n_cand], n_worlds[n_cand]
  * (the N each stopping rule chose).  Errors: IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM,
  * IMIN_EDEVICE. */
 int imin_final_estimates(imin_graph *g, const int32_t *S, int32_t nS, int32_t n_cand, const int32_t *const *B,
