@@ -169,9 +169,9 @@ int imin_sample(imin_graph *g, const int32_t *S, int32_t nS, const int32_t *bloc
  * serves every candidate.  On graphs of at least 2^18 nodes whose worlds keep their
  * visited structures in global memory, the traversal runs on a relabelled copy of the
  * forward index (nodes ordered by how often 2,048 worlds of a stream tag no estimate
- * draws reach them; each edge keeps its coin), which changes no value and takes about
- * 16 B per node + 40 B per edge of device memory while the call runs (imin_solve holds
- * it from its final estimates to its return).  spread_hint: the expected spread without
+ * draws reach them; each edge keeps its coin), which changes no value and takes at most
+ * 48 B per node + 9 B per edge of device memory while the call runs (imin_solve holds
+ * it from its final estimates to its return; 125 MB on a 1M-node, 8.5M-edge graph).  spread_hint: the expected spread without
  * blockers if known (sizes the traversal queue; 0 = unknown).  Outputs: I_after[n_cand], n_worlds[n_cand]
  * (the N each stopping rule chose).  Errors: IMIN_EINVAL, IMIN_ERANGE, IMIN_ENOMEM,
  * IMIN_EDEVICE. */
