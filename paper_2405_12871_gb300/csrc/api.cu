@@ -958,17 +958,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
             minb = std::min(m, b == 256 ? 8 : 4);
         }
     }
-    // with a relabelled index the map words of its first 32,768 labels (the nodes most
-    // often reached) live in shared memory (IMIN_FINAL_HOT=0 keeps the whole map in the
-    // slot; the split changes no result, only where a claim lands)
-    bool any_view = false;
-    for (const FinalSpec &f : specs) any_view |= f.hv && f.hv->on;
-    bool hot = any_view && bd == 256;
-    if (const char *he = std::getenv("IMIN_FINAL_HOT")) {
-        if (he[0] == '0') hot = false;
-        if (he[0] == '2' && bd == 256) hot = true;   // test hook: also on the original labels
-    }
-    const int occ = std::max(1, std::min(minb, final_blocks_per_sm(bd, hot)));
+    const int occ = std::max(1, std::min(minb, final_blocks_per_sm(bd)));
     // queue entries per slot: a world needs at most the three reach sets' sizes; the
     // queue holds 32 times the expected spread (all 3 (n + 1) when it is not known), and
     // a world that overflows it (the reach distribution has a long tail) is re-run one
@@ -1092,7 +1082,7 @@ FinalStats final_estimates(imin_ctx *ctx, std::vector<FinalSpec> &specs)
         IM_CUDA(cudaMemcpyAsync(dtasks.p, ht.data(), ht.size() * sizeof(FTask), cudaMemcpyHostToDevice,
                                 ctx->stream));
         IM_CUDA(cudaEventRecord(e0, ctx->stream));
-        launch_final_tasks(ctx, dtasks.as<FTask>(), nt, nmax, qcap, bd, hot, (int)ctas, ctx->slots_final.p,
+        launch_final_tasks(ctx, dtasks.as<FTask>(), nt, nmax, qcap, bd, (int)ctas, ctx->slots_final.p,
                            cd.as<uint32_t>(), cd.as<uint32_t>() + nt);
         IM_CUDA(cudaEventRecord(e1, ctx->stream));
         IM_CUDA(cudaEventSynchronize(e1));

@@ -264,11 +264,9 @@ struct FTask {
     uint32_t deferred_cap;
 };
 size_t final_slot_bytes(int32_t n, int32_t qcap, size_t *off_queue);
-// hot: the variant that keeps the map words of the first 32,768 labels in shared memory
-// (on the relabelled forward index, the nodes the query's worlds reach most often)
-int final_blocks_per_sm(int bd, bool hot);
+int final_blocks_per_sm(int bd);
 void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int32_t qcap, int bd,
-                        bool hot, int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
+                        int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done);
 
 // Global Sampling worlds traversed backwards from the target (gs_rev.cu): one warp per
 // world; worlds whose reverse set outgrows the warp's table are deferred (top bit).

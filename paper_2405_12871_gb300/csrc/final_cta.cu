@@ -46,27 +46,10 @@ struct FArgs {
     int l2_keep;
 };
 
-// The candidate map of a slot: words below HOTW (labels below 8 HOTW) in the CTA's
-// shared memory, the rest in the slot.  On the relabelled forward index those are the
-// nodes the query's worlds reach most often, and their claims stay on chip.
-extern __shared__ uint32_t final_hot[];
-
-template <int HOTW>
-struct Map {
-    uint32_t *g;
-    __device__ __forceinline__ uint32_t *at(int v) const
-    {
-        const int w = v >> 3;
-        if (HOTW > 0 && w < HOTW) return final_hot + w;
-        return g + w;
-    }
-};
-
 // One pass over one 4-edge group per lane: claim the live targets for the source's
 // candidate bits `om` and append the entries whose bits are new.  All lanes call it.
-template <int HOTW>
 __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int ob, int oe, uint32_t om,
-                                           const Coins &K, const Map<HOTW> nib, int32_t *Q, int *app, int tail,
+                                           const Coins &K, uint32_t *nib, int32_t *Q, int *app, int tail,
                                            int lane, uint32_t lt_mask, int qcap, int *ovf)
 {
     uint32_t live = 0;
@@ -74,10 +57,10 @@ __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int 
     if (act) live = op.live(it, ob, oe, K, c4);
     uint32_t n0 = 0, n1 = 0, n2 = 0, n3 = 0;
     const int s0 = (c4.x & 7) * 4, s1 = (c4.y & 7) * 4, s2 = (c4.z & 7) * 4, s3 = (c4.w & 7) * 4;
-    if (live & 1u) n0 = om & ~(atomicOr(nib.at(c4.x), om << s0) >> s0);
-    if (live & 2u) n1 = om & ~(atomicOr(nib.at(c4.y), om << s1) >> s1);
-    if (live & 4u) n2 = om & ~(atomicOr(nib.at(c4.z), om << s2) >> s2);
-    if (live & 8u) n3 = om & ~(atomicOr(nib.at(c4.w), om << s3) >> s3);
+    if (live & 1u) n0 = om & ~(atomicOr(&nib[c4.x >> 3], om << s0) >> s0);
+    if (live & 2u) n1 = om & ~(atomicOr(&nib[c4.y >> 3], om << s1) >> s1);
+    if (live & 4u) n2 = om & ~(atomicOr(&nib[c4.z >> 3], om << s2) >> s2);
+    if (live & 8u) n3 = om & ~(atomicOr(&nib[c4.w >> 3], om << s3) >> s3);
     const uint32_t b0 = __ballot_sync(IMIN_FULL, n0 != 0), b1 = __ballot_sync(IMIN_FULL, n1 != 0),
                    b2 = __ballot_sync(IMIN_FULL, n2 != 0), b3 = __ballot_sync(IMIN_FULL, n3 != 0);
     const int tot = __popc(b0) + __popc(b1) + __popc(b2) + __popc(b3);
@@ -100,8 +83,8 @@ __device__ __forceinline__ void pass_multi(const Fwd &op, bool act, int it, int 
 // Level-synchronous expansion of the packed queue Q[0, tail0), with the slice / hub
 // structure of the reach kernel (reach_cta.cuh, bfs): 32-entry slices per warp, hub
 // entries cut into pieces shared by the CTA.  Returns the final tail.
-template <int BD, int HOTW>
-__device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, const Map<HOTW> nib, int32_t *Q, int tail0,
+template <int BD>
+__device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, uint32_t *nib, int32_t *Q, int tail0,
                                          Shared<BD> &sh, unsigned long long &wedges, int qcap, int *ovf)
 {
     const int tid = threadIdx.x, lane = tid & 31;
@@ -220,7 +203,7 @@ __device__ __forceinline__ int bfs_multi(const Fwd &op, const Coins &K, const Ma
     return tail;
 }
 
-template <int BD, int MINB, int HOTW>
+template <int BD, int MINB>
 __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
 {
     __shared__ Shared<BD> sh;
@@ -230,8 +213,7 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
 
     const int tid = threadIdx.x, lane = tid & 31;
     char *slot = a.slot_base + (size_t)blockIdx.x * a.slot_bytes;
-    const Map<HOTW> nib{reinterpret_cast<uint32_t *>(slot)};
-    for (int w = tid; w < HOTW; w += BD) final_hot[w] = 0u;
+    uint32_t *const nib = reinterpret_cast<uint32_t *>(slot);
     int32_t *const Q = reinterpret_cast<int32_t *>(slot + a.off_queue);
     int ti = (int)(blockIdx.x % (unsigned)a.ntasks);
     for (;;) {
@@ -290,22 +272,21 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
             if ((mask >> c) & 1u)
                 for (int i = tid; i < T.nB[c]; i += BD) {
                     const int v = T.B[c][i];
-                    atomicOr(nib.at(v), (1u << c) << ((v & 7) * 4));
+                    atomicOr(&nib[v >> 3], (1u << c) << ((v & 7) * 4));
                 }
         for (int i = tid; i < nS; i += BD) {
             const int s = T.S[i];
-            atomicOr(nib.at(s), mask << ((s & 7) * 4));
+            atomicOr(&nib[s >> 3], mask << ((s & 7) * 4));
             Q[i] = (s << 3) | (int)mask;
         }
         __syncthreads();
         unsigned long long wedges = 0;
         const Fwd fwd{T.row_ptr, T.ce, reach_cta::graph_l2_policy(a.l2_keep != 0), T.rng, T.gid};
-        const int tail = bfs_multi<BD, HOTW>(fwd, K, nib, Q, nS, sh, wedges, a.qcap, &s_ovf);
+        const int tail = bfs_multi<BD>(fwd, K, nib, Q, nS, sh, wedges, a.qcap, &s_ovf);
         if (tail < 0) {
             // overflow: wipe the map (dropped entries left bits that the queue cannot
             // find) and list the world for the host
-            for (size_t w = tid; w < a.nib_words; w += BD) nib.g[w] = 0u;
-            for (int w = tid; w < HOTW; w += BD) final_hot[w] = 0u;
+            for (size_t w = tid; w < a.nib_words; w += BD) nib[w] = 0u;
             if (tid == 0) {
                 const uint32_t d = atomicAdd(T.n_deferred, 1u);
                 if (d < T.deferred_cap) T.deferred[d] = rel;
@@ -321,11 +302,11 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
             c0 += x & 1;
             c1 += (x >> 1) & 1;
             c2 += (x >> 2) & 1;
-            *nib.at(x >> 3) = 0u;
+            nib[(x >> 3) >> 3] = 0u;
         }
         for (int c = 0; c < 3; ++c)
             if ((mask >> c) & 1u)
-                for (int i = tid; i < T.nB[c]; i += BD) *nib.at(T.B[c][i]) = 0u;
+                for (int i = tid; i < T.nB[c]; i += BD) nib[T.B[c][i] >> 3] = 0u;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             c0 += __shfl_xor_sync(IMIN_FULL, c0, o);
@@ -354,26 +335,10 @@ __global__ void __launch_bounds__(BD, MINB) cta_final_kernel(const FArgs a)
     }
 }
 
-// shared-memory words of the candidate map's on-chip part (32,768 labels, 16 KB: with
-// the kernel's 8.3 KB of static shared memory, 8 CTAs of 256 threads still fit an SM)
-constexpr int kHotWords = 4096;
-
-// the variant with the on-chip part prefers the largest shared-memory carveout (set
-// once per process; it is part of the kernel's occupancy)
-inline void set_hot_attr()
-{
-    static bool done = false;
-    if (done) return;
-    IM_CUDA(cudaFuncSetAttribute(cta_final_kernel<256, 8, kHotWords>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared));
-    done = true;
-}
-
-template <int BD, int MINB, int HOTW>
+template <int BD, int MINB>
 void launch(cudaStream_t st, const FArgs &a, int blocks)
 {
-    if (HOTW > 0) set_hot_attr();
-    cta_final_kernel<BD, MINB, HOTW><<<blocks, BD, (size_t)HOTW * 4, st>>>(a);
+    cta_final_kernel<BD, MINB><<<blocks, BD, 0, st>>>(a);
     IM_CHECK_LAUNCH();
 }
 
@@ -392,7 +357,7 @@ size_t final_slot_bytes(int32_t n, int32_t qcap, size_t *off_queue)
 }
 
 void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t nmax, int32_t qcap, int bd,
-                        bool hot, int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done)
+                        int ctas, void *slot_base, uint32_t *d_claim, uint32_t *d_done)
 {
     final_cta::FArgs a;
     a.tasks = d_tasks;
@@ -405,25 +370,18 @@ void launch_final_tasks(imin_ctx *ctx, const FTask *d_tasks, int ntasks, int32_t
     a.nib_words = ((size_t)nmax + 7) / 8;
     const char *env = std::getenv("IMIN_L2_KEEP");
     a.l2_keep = (env && env[0] == '0') ? 0 : 1;
-    if (bd == 256 && hot)
-        final_cta::launch<256, 8, final_cta::kHotWords>(ctx->stream, a, ctas);
-    else if (bd == 256)
-        final_cta::launch<256, 8, 0>(ctx->stream, a, ctas);
+    if (bd == 256)
+        final_cta::launch<256, 8>(ctx->stream, a, ctas);
     else
-        final_cta::launch<512, 4, 0>(ctx->stream, a, ctas);
+        final_cta::launch<512, 4>(ctx->stream, a, ctas);
 }
 
-int final_blocks_per_sm(int bd, bool hot)
+int final_blocks_per_sm(int bd)
 {
     int nb = 0;
-    if (bd == 256 && hot) final_cta::set_hot_attr();
-    cudaError_t e =
-        bd == 256 ? (hot ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &nb, final_cta::cta_final_kernel<256, 8, final_cta::kHotWords>, 256,
-                               (size_t)final_cta::kHotWords * 4)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, final_cta::cta_final_kernel<256, 8, 0>,
-                                                                         256, 0))
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, final_cta::cta_final_kernel<512, 4, 0>, 512, 0);
+    cudaError_t e = bd == 256
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, final_cta::cta_final_kernel<256, 8>, 256, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, final_cta::cta_final_kernel<512, 4>, 512, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;

@@ -22,14 +22,12 @@ def ctx():
 
 @pytest.mark.parametrize("hooks", [{}, {"IMIN_STOP_CHUNK": "613"}, {"IMIN_FINAL_QCAP": "400"},
                                    {"IMIN_HOT_WORLDS": "1"}, {"IMIN_HOT_WORLDS": "6000"},
-                                   {"IMIN_REACH_SMEM": "0", "IMIN_AUTOTUNE": "0"},
-                                   {"IMIN_FINAL_HOT": "0"}, {"IMIN_FINAL_HOT": "2"}])
+                                   {"IMIN_REACH_SMEM": "0", "IMIN_AUTOTUNE": "0"}])
 def test_solve_on_view_equals_oracle(ctx, monkeypatch, hooks):
     """Final estimates on the view (forced on a 20K-node Chung-Lu graph): in several
     chunks, with queue overflows re-run one candidate at a time on the original labels,
-    with degenerate (1 world: two count values) and many (6,000) count values, without
-    the autotuner, with the whole candidate map in global memory, and with its on-chip
-    part also on the original labels; then the same solve without the view."""
+    with degenerate (1 world: two count values) and many (6,000) count values, and
+    without the autotuner; then the same solve without the view."""
     for k, v in hooks.items():
         monkeypatch.setenv(k, v)
     g = synth.chung_lu(20_000, 10.0, 2.1, seed=7)
@@ -85,21 +83,3 @@ def test_final_estimates_entry_point_on_view(ctx, monkeypatch):
     for c in range(3):
         wN, wI = og.stop_rule(S, cands[c], beta=0.1, dprime=1.0 / g.n, key=6, tag=5, inst=2)
         assert (N[c], I[c]) == (wN, wI), c
-
-
-def test_map_split_between_shared_and_global_memory(ctx, monkeypatch):
-    """A 60K-node graph: the map words of labels below 32,768 live in shared memory and
-    the rest in the slot, so both parts see claims; equal to the original labels with
-    the whole map in global memory, and to the oracle."""
-    g = synth.chung_lu(60_000, 10.0, 2.1, seed=9)
-    S = synth.seeds_top_outdeg(g, 20, 0.01, seed=10)
-    kw = dict(k=25, eps=0.3, delta=1.0 / g.n, key=5)
-    G = ctx.load_graph(g)
-    monkeypatch.setenv("IMIN_HOT_VIEW", "2")
-    on = G.solve(S, **kw)
-    monkeypatch.setenv("IMIN_HOT_VIEW", "0")
-    monkeypatch.setenv("IMIN_FINAL_HOT", "0")
-    off = G.solve(S, **kw)
-    G.free()
-    compare(on, off)
-    compare(on, oracle.OracleGraph.from_graph(g).solve(S, **kw))
