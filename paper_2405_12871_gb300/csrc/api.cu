@@ -815,22 +815,29 @@ HotStats maybe_hot_view(imin_ctx *ctx, const imin_graph *g, const Query &q, uint
         const long v = std::strtol(we, nullptr, 10);
         if (v >= 1 && v <= 6000) W0 = (uint32_t)v;
     }
-    DBuf counts;
-    counts.ensure(ctx, (size_t)g->n * 8);
-    IM_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)g->n * 8, ctx->stream));
-    TaskRun t;
-    t.g = g;
-    t.q = qdev(q, key, TAG_HOT, inst);
-    t.first = 0;
-    t.count = W0;
-    t.out.reach = counts.as<unsigned long long>();
-    std::vector<TaskRun *> tp{&t};
-    Runner run(ctx);
-    run.run(tp, WF_REACH);
-    hs.kernel_ms = run.kernel_ms;
-    hs.launches = (uint64_t)run.launches;
-    hs.launches += (uint64_t)hot_view_build(ctx, g, counts.as<unsigned long long>(), W0, q.dS.as<int32_t>(),
-                                            (int32_t)q.S.size(), hv);
+    // the view is an optimisation: without the memory for it the estimates run on the
+    // original index
+    try {
+        DBuf counts;
+        counts.ensure(ctx, (size_t)g->n * 8);
+        IM_CUDA(cudaMemsetAsync(counts.p, 0, (size_t)g->n * 8, ctx->stream));
+        TaskRun t;
+        t.g = g;
+        t.q = qdev(q, key, TAG_HOT, inst);
+        t.first = 0;
+        t.count = W0;
+        t.out.reach = counts.as<unsigned long long>();
+        std::vector<TaskRun *> tp{&t};
+        Runner run(ctx);
+        run.run(tp, WF_REACH);
+        hs.kernel_ms = run.kernel_ms;
+        hs.launches = (uint64_t)run.launches;
+        hs.launches += (uint64_t)hot_view_build(ctx, g, counts.as<unsigned long long>(), W0, q.dS.as<int32_t>(),
+                                                (int32_t)q.S.size(), hv);
+    } catch (const ImError &e) {
+        if (e.code != IMIN_ENOMEM) throw;
+        hv.release();
+    }
     return hs;
 }
 
@@ -844,7 +851,13 @@ int hot_view_blocked(imin_ctx *ctx, HotView &hv, const Query *const qb[3], const
         hv.boff[c] = tot;
         if (use[c]) tot += (int64_t)qb[c]->blocked.size();
     }
-    hv.B.ensure(ctx, (size_t)std::max<int64_t>(tot, 1) * 4);
+    try {
+        hv.B.ensure(ctx, (size_t)std::max<int64_t>(tot, 1) * 4);
+    } catch (const ImError &e) {
+        if (e.code != IMIN_ENOMEM) throw;
+        hv.release();
+        return 0;
+    }
     for (int c = 0; c < 3; ++c)
         if (use[c] && !qb[c]->blocked.empty())
         {
