@@ -257,6 +257,9 @@ typedef struct imin_result {
  * Sec. 5.3).  Stream tags: 0 spread estimate, 1/2 CP collections C1/C2,
  * 3/4 LRR collections L1/L2, 5 the final estimates of B_L, B_U and B_R (all
  * three on the same worlds: Algorithm 1, line 4, with common random numbers).
+ * Worlds of two more tags are drawn and change no result: 0xFFFFFFF0 times the
+ * launch shapes of a graph's first query (the autotuner), 0xFFFFFFF1 orders the
+ * labels of the relabelled index the final estimates traverse.
  *   S, nS   host int32[nS], distinct, in [0, n), nS >= 1
  *   k       1 <= k < n - nS
  *   eps     in (0, 1); delta in (0, 1) (the paper uses delta = 1/n)
