@@ -210,6 +210,12 @@ typedef struct imin_solve_opts {
     int32_t variant;        /* imin_variant */
     uint64_t fixed_theta;   /* 0 = the paper's stopping rules; otherwise LSBM and GSBM
                                use theta_0 = fixed_theta and a single iteration */
+    uint64_t pr_worlds;     /* Pr[s -> v] in OPT^L (Sec. 5.1) and LHGA (Sec. 5.3): 0 = the
+                               direct activation probability q(v) = 1 - prod over seed
+                               edges (u, v) of (1 - p_q(u, v)); > 0 = the reach frequency
+                               count(v) / pr_worlds over worlds [0, pr_worlds) of stream
+                               tag 6 (seeds S, nothing blocked); at most 2^31 - 1.  With
+                               it, OPT^L = 0 (no top-k node reached) is IMIN_ERANGE */
 } imin_solve_opts;
 
 /* Result of imin_solve.  The four arrays are caller-allocated with room for
@@ -256,7 +262,8 @@ typedef struct imin_result {
  * blockers from V \ S by Algorithm 1 (LSBM Algorithm 4, GSBM Sec. 5.2, LHGA
  * Sec. 5.3).  Stream tags: 0 spread estimate, 1/2 CP collections C1/C2,
  * 3/4 LRR collections L1/L2, 5 the final estimates of B_L, B_U and B_R (all
- * three on the same worlds: Algorithm 1, line 4, with common random numbers).
+ * three on the same worlds: Algorithm 1, line 4, with common random numbers),
+ * 6 the reach frequencies of opts->pr_worlds.
  * Worlds of two more tags are drawn and change no result: 0xFFFFFFF0 times the
  * launch shapes of a graph's first query (the autotuner), 0xFFFFFFF1 orders the
  * labels of the relabelled index the final estimates traverse.

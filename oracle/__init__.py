@@ -109,7 +109,7 @@ def lib():
         L.oracle_gsbm_theta_max.restype = C.c_double
         L.oracle_solve.argtypes = [C.c_void_p, _P(C.c_int32), C.c_int32, C.c_int32, C.c_double,
                                    C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint32,
-                                   C.c_int32, C.c_uint64, _P(C.c_int32), _P(C.c_int32),
+                                   C.c_int32, C.c_uint64, C.c_uint64, _P(C.c_int32), _P(C.c_int32),
                                    _P(C.c_int32), _P(C.c_int32), _P(OResult)]
         L.oracle_sample_useq.argtypes = [C.c_void_p, _P(C.c_int32), C.c_int32, _P(C.c_int32), C.c_int32,
                                          _P(C.c_int32), C.c_int32, C.c_uint64, C.c_uint64, C.c_uint32,
@@ -269,13 +269,19 @@ class OracleGraph:
         return [int(x) for x in B[:nb]], int(calls.value)
 
     def solve(self, S, k, eps, delta, beta=0.1, gamma=0.1, key=0, inst=0, variant="sandimin",
-              fixed_theta=0):
+              fixed_theta=0, pr_worlds=0):
+        """Algorithm 1; pr_worlds > 0 reads Pr[s -> v] (OPT^L, LHGA) as the reach
+        frequency over that many worlds of stream tag 6.  Raises ValueError when that
+        reading gives OPT^L = 0."""
         S = _i32(S)
         outs = [np.zeros(max(k, 1), np.int32) for _ in range(4)]
         r = OResult()
-        lib().oracle_solve(self._h, _ptr(S, C.c_int32), len(S), int(k), float(eps), float(delta),
-                           float(beta), float(gamma), int(key), int(inst), VARIANT[variant],
-                           int(fixed_theta), *[_ptr(o, C.c_int32) for o in outs], C.byref(r))
+        rc = lib().oracle_solve(self._h, _ptr(S, C.c_int32), len(S), int(k), float(eps), float(delta),
+                                float(beta), float(gamma), int(key), int(inst), VARIANT[variant],
+                                int(fixed_theta), int(pr_worlds), *[_ptr(o, C.c_int32) for o in outs],
+                                C.byref(r))
+        if rc == 2:
+            raise ValueError("OPT^L = 0: no top-k node of ON was reached in the pr_worlds worlds")
         d = r.as_dict()
         d["blockers"] = outs[0][: r.n_blockers].copy()
         d["B_L"] = outs[1][: r.nBL].copy()

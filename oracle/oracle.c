@@ -1018,8 +1018,8 @@ static void append_lrr_worlds(const OGraph *g, Work *w, const int32_t *S, int32_
 
 int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, double eps,
                  double delta, double beta, double gamma, uint64_t key, uint32_t inst,
-                 int32_t variant, uint64_t fixed_theta, int32_t *blockers, int32_t *BL,
-                 int32_t *BU, int32_t *BR, OResult *res)
+                 int32_t variant, uint64_t fixed_theta, uint64_t pr_worlds, int32_t *blockers,
+                 int32_t *BL, int32_t *BU, int32_t *BR, OResult *res)
 {
     memset(res, 0, sizeof(*res));
     int32_t n = g->n;
@@ -1058,11 +1058,25 @@ int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, do
             double pq = (double)g->thr[e] / 16777216.0;
             prod[v] = prod[v] * (1.0 - pq);
         }
+    double *pr = (double *)malloc(sizeof(double) * ((size_t)n + 1));
+    for (int32_t v = 0; v < n; ++v) pr[v] = 1.0 - prod[v];
+    /* The alternative reading: Pr[s -> v] as the fraction of the worlds
+     * 0 .. pr_worlds - 1 of stream tag 6 in which S reaches v. */
+    if (pr_worlds > 0) {
+        uint64_t *cnt = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+        for (uint64_t t = 0; t < pr_worlds; ++t) {
+            World wd = {NULL, key, t, 6u, inst};
+            int32_t R = world_reach(g, w, &wd, S, nS);
+            for (int32_t i = 0; i < R; ++i) cnt[w->queue[i]] += 1;
+        }
+        for (int32_t v = 0; v < n; ++v) pr[v] = (double)cnt[v] / (double)pr_worlds;
+        free(cnt);
+    }
     ScoreItem *byq = (ScoreItem *)malloc(sizeof(ScoreItem) * (size_t)nON);
     ScoreItem *bys = (ScoreItem *)malloc(sizeof(ScoreItem) * (size_t)nON);
     for (int32_t i = 0; i < nON; ++i) {
         int32_t v = ON[i];
-        double q = 1.0 - prod[v];
+        double q = pr[v];
         byq[i].score = q; byq[i].v = v;
         bys[i].score = q * (double)(g->row_ptr[v + 1] - g->row_ptr[v]); bys[i].v = v;
     }
@@ -1071,6 +1085,11 @@ int oracle_solve(const OGraph *g, const int32_t *S_in, int32_t nS, int32_t k, do
     double OPT = 0.0;
     for (int32_t i = 0; i < k; ++i) OPT += byq[i].score;
     res->OPT_L = OPT;
+    free(pr);
+    if (!(OPT > 0.0)) {                    /* no top-k node reached in any world */
+        free(byq); free(bys); free(prod); free(ON); free(inON); free(S); work_free(w);
+        return 2;
+    }
 
     /* LHGA (Sec. 5.3): top-k of ON by q(v) * outdeg(v) */
     for (int32_t i = 0; i < k; ++i) BR[i] = bys[i].v;

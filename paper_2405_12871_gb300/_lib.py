@@ -40,7 +40,8 @@ class SampleOut(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("beta", C.c_double), ("gamma", C.c_double), ("key", C.c_uint64),
-                ("inst", C.c_uint32), ("variant", C.c_int32), ("fixed_theta", C.c_uint64)]
+                ("inst", C.c_uint32), ("variant", C.c_int32), ("fixed_theta", C.c_uint64),
+                ("pr_worlds", C.c_uint64)]
 
 
 class Result(C.Structure):
@@ -235,14 +236,14 @@ def imin_sample(ctx, g, n, S, blocked=(), theta=1, key=0, tag=0, inst=0, first=0
 
 
 def imin_solve(ctx, g, S, k, eps, delta, beta=0.1, gamma=0.1, key=0, inst=0,
-               variant="sandimin", fixed_theta=0):
+               variant="sandimin", fixed_theta=0, pr_worlds=0):
     L = load()
     S = _as_i32(S)
     arrs = [np.zeros(max(int(k), 1), np.int32) for _ in range(4)]
     r = Result()
     r.blockers, r.B_L, r.B_U, r.B_R = [a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
     opts = SolveOpts(float(beta), float(gamma), int(key), int(inst), VARIANTS[variant],
-                     int(fixed_theta))
+                     int(fixed_theta), int(pr_worlds))
     rc = L.imin_solve(g, _i32p(S), len(S), int(k), float(eps), float(delta), C.byref(opts),
                       C.byref(r))
     _check(ctx, rc, "imin_solve")
@@ -275,7 +276,7 @@ def _result_dict(r, arrs):
 
 def imin_solve_batch(ctx, queries):
     """queries: list of dicts with keys g (graph handle), S, k, eps, delta and optional
-    beta, gamma, key, inst, variant, fixed_theta.  Returns one result dict per query."""
+    beta, gamma, key, inst, variant, fixed_theta, pr_worlds.  Returns one result dict per query."""
     L = load()
     n = len(queries)
     qs = (Query * max(n, 1))()
@@ -293,7 +294,8 @@ def imin_solve_batch(ctx, queries):
         qs[i].delta = float(q["delta"])
         qs[i].opts = SolveOpts(float(q.get("beta", 0.1)), float(q.get("gamma", 0.1)),
                                int(q.get("key", 0)), int(q.get("inst", 0)),
-                               VARIANTS[q.get("variant", "sandimin")], int(q.get("fixed_theta", 0)))
+                               VARIANTS[q.get("variant", "sandimin")], int(q.get("fixed_theta", 0)),
+                               int(q.get("pr_worlds", 0)))
         rs[i].blockers, rs[i].B_L, rs[i].B_U, rs[i].B_R = [
             a.ctypes.data_as(C.POINTER(C.c_int32)) for a in arrs]
     rc = L.imin_solve_batch(ctx, n, qs, rs)
@@ -439,7 +441,8 @@ class Server:
         q.delta = float(delta)
         q.opts = SolveOpts(float(kw.get("beta", 0.1)), float(kw.get("gamma", 0.1)),
                            int(kw.get("key", 0)), int(kw.get("inst", 0)),
-                           VARIANTS[kw.get("variant", "sandimin")], int(kw.get("fixed_theta", 0)))
+                           VARIANTS[kw.get("variant", "sandimin")], int(kw.get("fixed_theta", 0)),
+                           int(kw.get("pr_worlds", 0)))
         t = C.c_uint64()
         rc = L.imin_server_submit(self.h, C.byref(q), C.byref(t))
         _check(self.ctx.h, rc, "imin_server_submit")

@@ -876,6 +876,7 @@ int hot_view_blocked(imin_ctx *ctx, HotView &hv, const Query *const qb[3], const
 // stops at its own N, found exactly on the host from the per-world sizes.
 // ---------------------------------------------------------------------------
 constexpr uint32_t TAG_FINAL = 5u;
+constexpr uint32_t TAG_PR = 6u;   // worlds of the reach-frequency reading of Pr[s -> v]
 
 struct FinalSpec {
     const imin_graph *g;
@@ -1632,6 +1633,7 @@ struct Inst {
     int32_t k = 0;
     double eps = 0.0, delta = 0.0, beta = 0.0, gamma = 0.0;
     uint64_t key = 0, fixed_theta = 0;
+    uint64_t pr_worlds = 0;   // Pr[s -> v] reading: 0 = q(v), else reach frequency over that many worlds
     uint32_t inst = 0;
     int variant = 0;
     imin_result *res = nullptr;
@@ -1664,6 +1666,7 @@ void inst_prepare(imin_ctx *ctx, Inst &I, const int32_t *S_in, int32_t nS)
         !(I.beta > 0.0 && I.beta < 1.0) || !(I.gamma > 0.0 && I.gamma < 1.0))
         fail(IMIN_EINVAL, "eps, delta, beta and gamma must lie in (0, 1)");
     if (I.variant < IMIN_SANDIMIN || I.variant > IMIN_LHGA) fail(IMIN_EINVAL, "unknown variant");
+    if (I.pr_worlds >= ((uint64_t)1 << 31)) fail(IMIN_EINVAL, "pr_worlds must be below 2^31");
     const int32_t n = I.g->n, k = I.k;
     if (k < 1 || (int64_t)k >= (int64_t)n - nS) fail(IMIN_EINVAL, "k must satisfy 1 <= k < n - |S|");
     std::memset(res, 0, sizeof(*res));
@@ -1701,10 +1704,33 @@ void inst_prepare(imin_ctx *ctx, Inst &I, const int32_t *S_in, int32_t nS)
             const double pq = (double)g->h_thr[e] / 16777216.0;
             prod[v] = prod[v] * (1.0 - pq);
         }
+    std::vector<double> pr(n);
+    for (int32_t v = 0; v < n; ++v) pr[v] = 1.0 - prod[v];
+    // the alternative reading: Pr[s -> v] as the fraction of the worlds
+    // 0 .. pr_worlds - 1 of stream tag 6 in which S reaches v
+    if (I.pr_worlds > 0) {
+        DBuf cnt;
+        cnt.ensure(ctx, (size_t)n * 8);
+        IM_CUDA(cudaMemsetAsync(cnt.p, 0, (size_t)n * 8, ctx->stream));
+        TaskRun t;
+        t.g = g;
+        t.q = qdev(I.q, I.key, TAG_PR, I.inst);
+        t.first = 0;
+        t.count = (uint32_t)I.pr_worlds;
+        t.out.reach = cnt.as<unsigned long long>();
+        std::vector<TaskRun *> tp{&t};
+        Runner run(ctx);
+        run.run(tp, WF_REACH);
+        std::vector<unsigned long long> h((size_t)n);
+        IM_CUDA(cudaMemcpy(h.data(), cnt.p, (size_t)n * 8, cudaMemcpyDeviceToHost));
+        for (int32_t v = 0; v < n; ++v) pr[v] = (double)h[v] / (double)I.pr_worlds;
+        res->worlds_sampled += t.acc[4];
+        res->edges_scanned += t.acc[1];
+    }
     std::vector<ScoreItem> byq(I.ON.size()), bys(I.ON.size());
     for (size_t i = 0; i < I.ON.size(); ++i) {
         const int32_t v = I.ON[i];
-        const double qv = 1.0 - prod[v];
+        const double qv = pr[v];
         byq[i] = {qv, v};
         bys[i] = {qv * (double)(g->h_row_ptr[v + 1] - g->h_row_ptr[v]), v};
     }
@@ -1715,6 +1741,7 @@ void inst_prepare(imin_ctx *ctx, Inst &I, const int32_t *S_in, int32_t nS)
     for (int32_t i = 0; i < k; ++i) OPT += byq[i].score;
     I.OPT = OPT;
     res->OPT_L = OPT;
+    if (!(OPT > 0.0)) fail(IMIN_ERANGE, "OPT^L = 0: no top-k node of ON was reached in the pr_worlds worlds");
     I.BRv.resize(k);
     for (int32_t i = 0; i < k; ++i) I.BRv[i] = bys[i].v;
     I.do_L = I.variant == IMIN_SANDIMIN || I.variant == IMIN_SANDIMIN_MINUS || I.variant == IMIN_LSBM;
@@ -2580,6 +2607,7 @@ int imin_solve_batch(imin_ctx *ctx, int32_t n_inst, const imin_query *queries, i
             I.inst = qq.opts.inst;
             I.variant = qq.opts.variant;
             I.fixed_theta = qq.opts.fixed_theta;
+            I.pr_worlds = qq.opts.pr_worlds;
             I.res = &results[i];
             I.blockers = results[i].blockers;
             I.B_L = results[i].B_L;
@@ -2777,6 +2805,7 @@ int imin_server_submit(imin_server *srv, const imin_query *q, uint64_t *ticket)
     I.inst = q->opts.inst;
     I.variant = q->opts.variant;
     I.fixed_theta = q->opts.fixed_theta;
+    I.pr_worlds = q->opts.pr_worlds;
     I.res = &j->res;
     I.blockers = j->res.blockers;
     I.B_L = j->res.B_L;

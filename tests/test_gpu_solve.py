@@ -256,3 +256,29 @@ def test_explicit_autotune_changes_nothing(ctx):
     assert G.tuning() == t
     G.free()
     compare(a, oracle.OracleGraph.from_graph(g).solve(S, **kw))
+
+
+def test_reach_frequency_reading_of_pr(ctx):
+    """Pr[s -> v] in OPT^L and LHGA read as the reach frequency over 2,000 worlds of
+    stream tag 6 (imin_solve_opts.pr_worlds): equal to the oracle on ER-1K and on a
+    20K-node Chung-Lu graph; OPT^L = 0 is IMIN_ERANGE on both sides."""
+    from paper_2405_12871_gb300 import _lib
+    import pin_graphs
+    g1, S1, cfg = synth.workload_er1k()
+    g2 = synth.chung_lu(20_000, 10.0, 2.1, seed=3)
+    S2 = synth.seeds_top_outdeg(g2, 10, 0.01, seed=4)
+    cases = [(g1, S1, dict(k=cfg["k"], eps=0.2, delta=1.0 / g1.n, key=1)),
+             (g2, S2, dict(k=20, eps=0.3, delta=1.0 / g2.n, key=3))]
+    for g, S, kw in cases:
+        G = ctx.load_graph(g)
+        og = oracle.OracleGraph.from_graph(g)
+        got = G.solve(S, pr_worlds=2000, **kw)
+        compare(got, og.solve(S, pr_worlds=2000, **kw))
+        assert got["OPT_L"] != G.solve(S, **kw)["OPT_L"]
+        G.free()
+    h = pin_graphs.graph(4, [(0, 1, 2.0 ** -20), (0, 2, 2.0 ** -20), (2, 3, 0.5)])
+    H = ctx.load_graph(h)
+    with pytest.raises(_lib.IminError) as e:
+        H.solve([0], k=1, eps=0.5, delta=0.1, fixed_theta=100, pr_worlds=1)
+    assert e.value.code == _lib.IMIN_ERANGE
+    H.free()

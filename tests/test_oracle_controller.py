@@ -14,6 +14,9 @@ gives a different answer:
 * LHGA ranks ON by q(v) * outdeg(v), ties to the smaller id.  The graph makes the top
   two differ from the top two by q alone, by out-degree alone and by q * in-degree,
   and node 1 ties node 2 on the score while node 2 has the larger q.
+* The alternative reading of Pr[s -> v] (the reach frequency over worlds of stream
+  tag 6): a node reached directly and through another node, where the two readings
+  give 0.5 and about 0.75.
 * ratio_lb = ((1 - gamma)^2 / (1 + gamma)^2) (1 - 1/e - eps) (I_hat - I_after[U]) / D^U_hat
   on a p = 1 graph, where every LRR set contains node 1, so B_U = {1}, D^U_hat = |V'_s|
   exactly, D^L({1}) = 3 != D^U({1}) = 5, and both stopping-rule estimates have the
@@ -136,3 +139,44 @@ def test_ratio_lower_bound_absent_without_the_upper_candidate():
     og = oracle.OracleGraph.from_graph(pin_graphs.ratio_graph())
     r = og.solve([0], k=1, eps=0.2, delta=0.05, variant="sandimin-")
     assert r["ratio_lb"] == 0.0 and r["DU_hat"] == 0.0
+
+
+# ------------------------------------- Pr[s -> v] as the reach frequency (Sec. 5.1)
+
+def _two_path_graph():
+    # s = 0 -> 1 (p = 0.5), 0 -> 2 (p = 0.5), 1 -> 2 (p = 1), plus node 3 reached from 2
+    # (so that |ON| = 2 > k = 1 and the solve runs).  Direct activation q(2) = 0.5, but
+    # Pr[s -> 2] = 1 - 0.5 * 0.5 = 0.75 (through node 1 as well).
+    return pin_graphs.graph(4, [(0, 1, 0.5), (0, 2, 0.5), (1, 2, 1.0), (2, 3, 0.5)])
+
+
+def test_opt_lower_with_reach_frequency():
+    """With pr_worlds = theta, OPT^L (k = 1) is the reach frequency of node 2 over the
+    worlds 0 .. theta - 1 of stream tag 6: near 0.75 (the two-path probability, 5 sigma),
+    where the direct-activation reading gives exactly 0.5; theta OPT^L is an integer
+    equal to node 2's reach count from the oracle's sampling routine on those worlds."""
+    og = oracle.OracleGraph.from_graph(_two_path_graph())
+    theta = 20_000
+    kw = dict(k=1, eps=0.5, delta=0.1, fixed_theta=500, key=3, inst=1)
+    direct = og.solve([0], **kw)
+    freq = og.solve([0], pr_worlds=theta, **kw)
+    assert direct["OPT_L"] == 0.5
+    sigma = math.sqrt(0.75 * 0.25 / theta)
+    assert abs(freq["OPT_L"] - 0.75) < 5 * sigma
+    cnt = freq["OPT_L"] * theta
+    assert cnt == round(cnt)
+    r = og.sample([0], theta=theta, key=3, tag=6, inst=1)
+    assert int(r["reach"][2]) == int(round(cnt))
+    assert int(r["reach"][1]) < int(r["reach"][2])
+    # LHGA (out-degree 1 for both): the direct reading ties 0.5 * 1 = 0.5 * 1 and takes
+    # the smaller id; the reach frequency ranks node 2 (about 0.75) first
+    assert list(direct["B_R"]) == [1]
+    assert list(freq["B_R"]) == [2]
+
+
+def test_reach_frequency_zero_opt_is_an_error():
+    """One world where no out-neighbour of S is reached: OPT^L = 0 cannot bound theta_max."""
+    g = pin_graphs.graph(4, [(0, 1, 2.0 ** -20), (0, 2, 2.0 ** -20), (2, 3, 0.5)])
+    og = oracle.OracleGraph.from_graph(g)
+    with pytest.raises(ValueError):
+        og.solve([0], k=1, eps=0.5, delta=0.1, fixed_theta=100, pr_worlds=1)
