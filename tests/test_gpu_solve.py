@@ -269,13 +269,17 @@ def test_reach_frequency_reading_of_pr(ctx):
     S2 = synth.seeds_top_outdeg(g2, 10, 0.01, seed=4)
     cases = [(g1, S1, dict(k=cfg["k"], eps=0.2, delta=1.0 / g1.n, key=1)),
              (g2, S2, dict(k=20, eps=0.3, delta=1.0 / g2.n, key=3))]
+    differ = []
     for g, S, kw in cases:
         G = ctx.load_graph(g)
         og = oracle.OracleGraph.from_graph(g)
         got = G.solve(S, pr_worlds=2000, **kw)
         compare(got, og.solve(S, pr_worlds=2000, **kw))
-        assert got["OPT_L"] != G.solve(S, **kw)["OPT_L"]
+        differ.append(got["OPT_L"] != G.solve(S, **kw)["OPT_L"])
         G.free()
+    # on ER-1K the two readings give different OPT^L; on the Chung-Lu graph the top 20
+    # out-neighbours have in-degree 1 (p = 1), so both give 20
+    assert differ[0]
     h = pin_graphs.graph(4, [(0, 1, 2.0 ** -20), (0, 2, 2.0 ** -20), (2, 3, 0.5)])
     H = ctx.load_graph(h)
     with pytest.raises(_lib.IminError) as e:
